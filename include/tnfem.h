@@ -1,0 +1,235 @@
+/*
+ * tnfem.h -- C ABI of the GB300 tensor-network FEM solver for linear elasticity.
+ *
+ * The library solves the Galerkin system A u = f of isotropic linear elasticity discretised
+ * with Q1 (2D) / trilinear (3D) elements on a tensor grid of 2^levels nodes per axis
+ * (Section 3, Eq. femsys; Section 5), with A, f and u held in the quantized tensor-train
+ * (QTT) layout of Section 5.2: a component core of mode D first, then one core per level of
+ * mode 2^D that carries that level's bit of every axis, most significant level first
+ * (Section 4).  The solve is the AMEn sweep named in Section 5.4 / Algorithm 2.
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every call returns a tnfem_status and never aborts, exits or traps.  On failure
+ *    tnfem_last_error(ctx) holds a one-line message (per context).
+ *  - Ownership: handles (tnfem_ctx, tnfem_mpo, tnfem_tt) are created by the library and freed
+ *    by the caller with the matching tnfem_*_destroy / tnfem_free_* call.  Host buffers passed
+ *    in belong to the caller and are never retained after the call returns.  Device pointers
+ *    passed to the tnfem_op_* kernel entry points belong to the caller as well.
+ *  - Threading: a context is used by one host thread at a time.
+ *  - Units: SI.  The grid spans the box [lo, hi]; node index (i, j[, k]) in [0, 2^levels)^D.
+ *  - Precision: unless a call says otherwise, data crossing the boundary is IEEE binary64.
+ *  - Core layouts (all row-major, last index fastest, no padding):
+ *      vector core  [r_{k-1}][n_k][r_k]
+ *      operator core [a_{k-1}][n_k (row, test)][n_k (column, trial)][a_k]
+ */
+#ifndef TNFEM_H
+#define TNFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNFEM_OK = 0,
+  TNFEM_E_INVALID = 1,        /* bad argument: null pointer, size out of range, shape mismatch */
+  TNFEM_E_NOMEM = 2,          /* device or host allocation failed */
+  TNFEM_E_CUDA = 3,           /* a CUDA runtime call failed (message holds the CUDA error) */
+  TNFEM_E_NOT_CONVERGED = 4,  /* solve stopped at max_sweeps / max_refine; result still filled */
+  TNFEM_E_TIMEOUT = 5,        /* a bounded device-side wait ran out */
+  TNFEM_E_BUDGET = 6,         /* request exceeds the context's device-memory budget */
+  TNFEM_E_NUMERIC = 7         /* NaN/Inf or a breakdown (non-positive curvature) was detected */
+} tnfem_status;
+
+typedef struct tnfem_ctx tnfem_ctx;
+typedef struct tnfem_mpo tnfem_mpo;
+typedef struct tnfem_tt tnfem_tt;
+
+/* Faces: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z. */
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int levels;          /* L >= 1: 2^L nodes per axis, boundary nodes included (Section 5) */
+  double lo[3], hi[3]; /* box corners; only the first dim entries are read */
+  int clamped[6];      /* 1: homogeneous Dirichlet on all components of that face, 0: traction face */
+  int plane_stress;    /* 2D only: 1 uses the modified Lame parameter lambda* = 2 lambda mu/(lambda+2 mu) */
+} tnfem_grid;
+
+typedef struct {
+  double E[2];    /* Young's modulus; E[0] for elements whose centroid has x < split_x, E[1] otherwise */
+  double split_x; /* set to a value beyond hi[0] (e.g. 1e300) for a homogeneous material */
+  double nu;      /* Poisson's ratio, 0 <= nu < 0.5 */
+} tnfem_material;
+
+typedef enum {
+  TNFEM_LOAD_GRAVITY = 0,      /* body force (0, -rho g) in 2D, (0, 0, -rho g) in 3D */
+  TNFEM_LOAD_TRACTION = 1,     /* uniform traction vector on face `face` */
+  TNFEM_LOAD_FOURIER = 2,      /* f_c(x) = scale * sum_m amp[c*n_modes+m] sin(pi wave_m . x + phase_m) */
+  TNFEM_LOAD_MANUFACTURED = 3  /* 2D unit square: body force and free-face tractions of
+                                  u* = (sin(pi x) sin(pi y), x(1-x) y(1-y)) */
+} tnfem_load_kind;
+
+typedef struct {
+  int kind;             /* tnfem_load_kind */
+  double rho, g;        /* GRAVITY */
+  int face;             /* TRACTION */
+  double traction[3];   /* TRACTION */
+  int n_modes;          /* FOURIER: number of modes */
+  const double* amp;    /* FOURIER: [dim][n_modes] host array */
+  const int* wave;      /* FOURIER: [n_modes][dim] host array of integer wave numbers */
+  const double* phase;  /* FOURIER: [n_modes] host array */
+  double scale;         /* FOURIER */
+} tnfem_load;
+
+typedef enum { TNFEM_FP64 = 0, TNFEM_MIXED = 1 } tnfem_precision;
+
+typedef struct {
+  double tol;          /* sweep stop: largest local residual or local update <= tol; truncation
+                          threshold tol/sqrt(ncores) (relative Frobenius) */
+  int rank_cap;        /* maximum TT rank of the solution (before enrichment) */
+  int kickrank;        /* rank of the residual enrichment (AMEn), >= 0 */
+  int max_sweeps;      /* per (inner) solve */
+  int precision;       /* tnfem_precision */
+  double refine_tol;   /* MIXED: stop refinement when ||e||_A / ||u||_A <= refine_tol */
+  int max_refine;      /* MIXED: maximum outer refinement steps */
+  uint64_t seed;       /* seed of the counter-based generator for the start guess / enrichment */
+  int local_maxit;     /* cap on conjugate-gradient iterations per local solve */
+} tnfem_solve_opts;
+
+typedef struct {
+  int sweeps;          /* total sweeps over all (inner) solves */
+  int refines;         /* outer refinement steps (MIXED), 0 for FP64 */
+  int max_rank;        /* largest bond rank of u */
+  long long local_iters; /* conjugate-gradient iterations over the whole solve */
+  double max_res;      /* largest local residual of the last sweep */
+  double max_dx;       /* largest relative local update of the last sweep */
+  double energy_err_est; /* MIXED: last ||e||_A / ||u||_A; FP64: 0 */
+  double t_solve_ms;   /* wall time of the solve (device-synchronised) */
+  double flops;        /* algorithmic flops counted by the sweep's contractions */
+  size_t bytes_A, bytes_f, bytes_u; /* storage of the operator, load and solution cores */
+  int converged;       /* 1 when the stopping rule fired */
+} tnfem_solve_info;
+
+/* ---- context ------------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t (may be NULL for the
+ * legacy default stream); all device work of this context is enqueued on it.  The optional
+ * allocator callbacks route every device allocation of the context (e.g. into a framework's
+ * caching allocator); when alloc_fn is NULL the library calls cudaMalloc/cudaFree itself. */
+typedef void* (*tnfem_alloc_fn)(size_t bytes, void* user);
+typedef void (*tnfem_free_fn)(void* ptr, void* user);
+tnfem_status tnfem_create(int device, void* stream, tnfem_alloc_fn alloc_fn, tnfem_free_fn free_fn,
+                          void* user, tnfem_ctx** out);
+void tnfem_destroy(tnfem_ctx* ctx);
+const char* tnfem_last_error(const tnfem_ctx* ctx);
+tnfem_status tnfem_set_stream(tnfem_ctx* ctx, void* stream);
+/* Number of kernels this context has launched since creation (for accounting). */
+long long tnfem_kernel_launches(const tnfem_ctx* ctx);
+
+/* ---- assembly (Algorithm 1, Section 5.2 / 5.3) ------------------------------------------- */
+
+/* Stiffness TT-operator with boundary conditions applied (Algorithm 1): A = P A0 P + s (I - P),
+ * P the projector onto unknowns off the clamped faces, s the mean over components of A0's
+ * diagonal at grid node (1,...,1).  Built on the host as exact Kronecker sums of 1D QTT
+ * matrices (axis-aligned box => constant Jacobian, Section 5.1), then rounded on the device to
+ * relative accuracy 1e-14.  Errors: TNFEM_E_INVALID for dim not in {2,3}, levels < 1 or > 20,
+ * degenerate box, nu out of [0, 0.5). */
+tnfem_status tnfem_build_stiffness(tnfem_ctx* ctx, const tnfem_grid* grid,
+                                   const tnfem_material* mat, tnfem_mpo** out);
+
+/* Mass TT-operator I_D (x) M_1D (x) ... (x) M_1D without boundary conditions (Section 5.3). */
+tnfem_status tnfem_build_mass(tnfem_ctx* ctx, const tnfem_grid* grid, tnfem_mpo** out);
+
+/* Load TT f = P (M f0 + sum_faces M_face t0) (Section 5.3), summed over n_loads loads and
+ * rounded on the device to relative accuracy 1e-14. */
+tnfem_status tnfem_build_load(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfem_material* mat,
+                              const tnfem_load* loads, int n_loads, tnfem_tt** out);
+
+/* ---- solve (Algorithm 2) ----------------------------------------------------------------- */
+
+/* Solve A u = f by AMEn (Section 5.4).  x0 may be NULL (a seeded rank-2 start is used).
+ * FP64: every contraction, local solve, QR and SVD in binary64.
+ * MIXED: inner AMEn solves of the correction equation in binary32, outer iterative refinement
+ * with binary64 residual projections and binary64 rounding of u + e.
+ * On TNFEM_E_NOT_CONVERGED *u and *info are still filled with the last iterate. */
+tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f,
+                         const tnfem_solve_opts* opts, const tnfem_tt* x0, tnfem_tt** u,
+                         tnfem_solve_info* info);
+
+/* ---- evaluation -------------------------------------------------------------------------- */
+
+/* Displacement at n grid nodes: nodes is a host array [n][dim] of node indices, out a host
+ * array [n][dim].  Each value is the product of core slices along the train. */
+tnfem_status tnfem_eval_displacement(tnfem_ctx* ctx, const tnfem_tt* u, const int64_t* nodes,
+                                     int64_t n, double* out);
+
+/* Small-strain tensor eps = sym(grad u) at the centres of n elements (element index = its
+ * lowest-corner node, each index in [0, 2^levels - 1)), from the element's nodal values and the
+ * Q1/trilinear shape gradients.  out: host [n][3] (xx, yy, xy) in 2D, [n][6] (xx,yy,zz,yz,xz,xy)
+ * in 3D. */
+tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_grid* grid,
+                               const int64_t* elems, int64_t n, double* out);
+
+/* Energy norm ||u - v||_A (v may be NULL for ||u||_A), computed on the explicitly formed and
+ * orthogonalised difference so that the result does not cancel. */
+tnfem_status tnfem_energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u,
+                               const tnfem_tt* v, double* out);
+
+/* <x, y> and ||x|| (norm from the orthogonalised train). */
+tnfem_status tnfem_tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y, double* out);
+tnfem_status tnfem_tt_norm(tnfem_ctx* ctx, const tnfem_tt* x, double* out);
+
+/* ---- tensor-train algebra ---------------------------------------------------------------- */
+
+/* TT rounding (a11): left-orthogonalise by Householder QR, then truncated SVDs right to left
+ * with threshold eps/sqrt(ncores-1) * ||x|| per bond and rank cap rmax (Section 4, Eq. qr). */
+tnfem_status tnfem_tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax, tnfem_tt** out);
+/* z = x + beta * y (exact, ranks add). */
+tnfem_status tnfem_tt_axpy(tnfem_ctx* ctx, const tnfem_tt* x, double beta, const tnfem_tt* y,
+                           tnfem_tt** out);
+/* y = A x exactly (ranks multiply). */
+tnfem_status tnfem_mpo_apply(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* x, tnfem_tt** out);
+
+/* Import / export of trains through host memory.  Export with cores == NULL fills ncores,
+ * ranks (ncores+1 entries) and modes (ncores entries) so the caller can size `cores`;
+ * ranks/modes must then hold at least 64 / 63 entries.  `cores` is the concatenation of the
+ * cores in order, each in the layout given at the top of this file. */
+tnfem_status tnfem_tt_export(tnfem_ctx* ctx, const tnfem_tt* x, int* ncores, int* ranks,
+                             int* modes, double* cores);
+tnfem_status tnfem_tt_import(tnfem_ctx* ctx, int ncores, const int* ranks, const int* modes,
+                             const double* cores, tnfem_tt** out);
+tnfem_status tnfem_mpo_export(tnfem_ctx* ctx, const tnfem_mpo* A, int* ncores, int* ranks,
+                              int* modes, double* cores);
+tnfem_status tnfem_mpo_import(tnfem_ctx* ctx, int ncores, const int* ranks, const int* modes,
+                              const double* cores, tnfem_mpo** out);
+void tnfem_free_tt(tnfem_tt* x);
+void tnfem_free_mpo(tnfem_mpo* A);
+
+/* ---- kernel-level entry points (device pointers, for parity tests of single sweep steps) ---- *
+ * All pointers are device pointers to binary64 arrays in the layouts stated; the work is
+ * enqueued on the context's stream and the call synchronises before returning.              */
+
+/* a4: local matvec y[a',i,b'] = sum PhiL[a',beta,a] A[beta,i,j,g] PhiR[b',g,b] x[a,j,b].
+ * PhiL [r0][a0][r0], A [a0][n][n][a1], PhiR [r1][a1][r1], x and y [r0][n][r1]. */
+tnfem_status tnfem_op_local_matvec(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1,
+                                   const double* PhiL, const double* A, const double* PhiR,
+                                   const double* x, double* y);
+/* a2/a8: left environment Phi'[b',g,b] = sum y[a',i,b'] Phi[a',beta,a] A[beta,i,j,g] x[a,j,b].
+ * Phi [ry0][a0][rx0], y [ry0][n][ry1], A [a0][n][n][a1], x [rx0][n][rx1], out [ry1][a1][rx1]. */
+tnfem_status tnfem_op_env_left(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx1, int n, int a0,
+                               int a1, const double* Phi, const double* y, const double* A,
+                               const double* x, double* out);
+/* Reduced Householder QR of an m x n row-major matrix: Q [m][k], R [k][n], k = min(m, n),
+ * diag(R) >= 0 is not enforced (Householder signs). */
+tnfem_status tnfem_op_qr(tnfem_ctx* ctx, int m, int n, const double* Ain, double* Q, double* R);
+/* Thin SVD by one-sided Jacobi of an m x n row-major matrix (m >= n): U [m][n] with unit
+ * columns, S [n] descending, Vt [n][n].  Each column pair of U is signed so that its entry of
+ * largest magnitude is positive. */
+tnfem_status tnfem_op_svd(tnfem_ctx* ctx, int m, int n, const double* Ain, double* U, double* S,
+                          double* Vt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNFEM_H */

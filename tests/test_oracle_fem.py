@@ -1,0 +1,196 @@
+"""Pins of oracle A (sparse Q1/trilinear FEM) against facts fixed outside the oracle.
+
+Each test targets a plausible mistake: a wrong Lame formula, a transposed coupling block, a
+dropped term in the element matrix, a sign error in the manufactured force, a wrong mass
+scaling, a BC that leaks into the solution, or an assembly that breaks convergence rates.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fem
+from paper_2501_12151_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_lame_closed_forms():
+    # plane strain: lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)); E=1, nu=0.25 -> 0.4, 0.4
+    lam, mu = fem.lame(1.0, 0.25, 2, False)
+    assert lam == pytest.approx(0.4, rel=1e-15)
+    assert mu == pytest.approx(0.4, rel=1e-15)
+    # plane stress (Section 2, modified Lame parameter): lambda* = E nu / (1 - nu^2)
+    lam_s, mu_s = fem.lame(1.0, 0.25, 2, True)
+    assert lam_s == pytest.approx(0.25 / (1 - 0.0625), rel=1e-14)
+    assert mu_s == pytest.approx(0.4, rel=1e-15)
+
+
+def test_element_matrix_matches_published_plane_stress_square():
+    """Unit-square Q1 plane-stress element stiffness against the closed form published with
+    the 88-line topology-optimisation code (Andreassen et al., 2011), thickness 1."""
+    E, nu = 1.0, 0.3
+    lam, mu = fem.lame(E, nu, 2, True)
+    X = fem.ref_corners(2).astype(float)          # corners (0,0),(0,1),(1,0),(1,1)
+    K, _ = fem.element_matrices(X, lam, mu)
+    k = [1 / 2 - nu / 6, 1 / 8 + nu / 8, -1 / 4 - nu / 12, -1 / 8 + 3 * nu / 8,
+         -1 / 4 + nu / 12, -1 / 8 - nu / 8, nu / 6, 1 / 8 - 3 * nu / 8]
+    idx = [[0, 1, 2, 3, 4, 5, 6, 7], [1, 0, 7, 6, 5, 4, 3, 2], [2, 7, 0, 5, 6, 3, 4, 1],
+           [3, 6, 5, 0, 7, 2, 1, 4], [4, 5, 6, 7, 0, 1, 2, 3], [5, 4, 3, 2, 1, 0, 7, 6],
+           [6, 3, 4, 1, 2, 7, 0, 5], [7, 2, 1, 4, 3, 6, 5, 0]]
+    KE = E / (1 - nu * nu) * np.array([[k[j] for j in row] for row in idx])
+    # published node order: lower-left, lower-right, upper-right, upper-left (x, y per node);
+    # ours: corner a = 2*b_x + b_y -> (0,0)=0, (1,0)=2, (1,1)=3, (0,1)=1
+    order = [0, 2, 3, 1]
+    perm = [2 * a + c for a in order for c in range(2)]
+    np.testing.assert_allclose(K[np.ix_(perm, perm)], KE, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,levels", [(2, 3), (3, 2)])
+def test_rigid_body_modes_in_kernel(dim, levels):
+    g = W.Grid(dim=dim, levels=levels, lo=(0.1, -0.2, 0.3), hi=(1.3, 0.7, 1.1))
+    A, _ = fem.assemble(g, W.Material(E=(3.0, 3.0), nu=0.3))
+    P = fem.nodal_points(g)
+    N = P.shape[0]
+    modes = []
+    for c in range(dim):
+        v = np.zeros((dim, N))
+        v[c] = 1.0
+        modes.append(v.ravel())
+    pairs = [(0, 1)] if dim == 2 else [(0, 1), (1, 2), (0, 2)]
+    for a, b in pairs:
+        v = np.zeros((dim, N))
+        v[a] = -P[:, b]
+        v[b] = P[:, a]
+        modes.append(v.ravel())
+    scale = abs(A).max()
+    for v in modes:
+        assert np.abs(A @ v).max() <= 1e-12 * scale * np.abs(v).max()
+    assert np.abs(A - A.T).max() <= 1e-15 * scale
+
+
+def test_patch_test_affine_field():
+    """An affine displacement has constant strain: interior rows of A u vanish."""
+    g = W.Grid(dim=2, levels=3)
+    A, _ = fem.assemble(g, W.Material(E=(1.0, 1.0), nu=0.3))
+    P = fem.nodal_points(g)
+    u = np.concatenate([0.3 + 1.1 * P[:, 0] - 0.4 * P[:, 1], -0.2 + 0.7 * P[:, 0] + 0.5 * P[:, 1]])
+    r = (A @ u).reshape(2, g.n, g.n)
+    assert np.abs(r[:, 1:-1, 1:-1]).max() < 1e-13
+
+
+@pytest.mark.parametrize("dim,levels", [(2, 3), (3, 2)])
+def test_mass_matrix_integrates_constants(dim, levels):
+    lo, hi = (0.0, -1.0, 2.0), (2.0, 0.5, 2.5)
+    g = W.Grid(dim=dim, levels=levels, lo=lo, hi=hi)
+    _, M = fem.assemble(g, W.Material())
+    N = g.n ** dim
+    vol = np.prod([hi[d] - lo[d] for d in range(dim)])
+    for c in range(dim):
+        e = np.zeros(dim * N)
+        e[c * N:(c + 1) * N] = 1.0
+        assert e @ (M @ e) == pytest.approx(vol, rel=1e-13)
+    # face mass integrates the face area
+    for face in range(2 * dim):
+        Mf = fem.face_mass(g, face)
+        d = face // 2
+        area = np.prod([hi[e] - lo[e] for e in range(dim) if e != d])
+        e = np.zeros(dim * N)
+        e[:N] = 1.0
+        assert e @ (Mf @ e) == pytest.approx(area, rel=1e-13)
+
+
+def test_manufactured_force_is_minus_div_sigma():
+    """The hand-derived body force equals -div sigma(u*) by central differences of sigma."""
+    lam, mu = 1.7, 0.9
+    x, y = np.array([0.23, 0.61, 0.87]), np.array([0.41, 0.13, 0.77])
+    h = 1e-5
+    sx1 = fem.manufactured_stress(x + h, y, lam, mu)
+    sx0 = fem.manufactured_stress(x - h, y, lam, mu)
+    sy1 = fem.manufactured_stress(x, y + h, lam, mu)
+    sy0 = fem.manufactured_stress(x, y - h, lam, mu)
+    div1 = (sx1[0] - sx0[0]) / (2 * h) + (sy1[2] - sy0[2]) / (2 * h)
+    div2 = (sx1[2] - sx0[2]) / (2 * h) + (sy1[1] - sy0[1]) / (2 * h)
+    f1, f2 = fem.manufactured_force(x, y, lam, mu)
+    np.testing.assert_allclose(f1, -div1, rtol=1e-7)
+    np.testing.assert_allclose(f2, -div2, rtol=1e-7)
+
+
+def test_manufactured_convergence_rates():
+    """Optimal rates: ||u* - u_h||_L2 = O(h^2), ||u* - u_h||_a = O(h)."""
+    Ls = [3, 4, 5, 6, 7]
+    l2, en, hs = [], [], []
+    for L in Ls:
+        pr = W.manufactured_2d(L)
+        Abc, f = fem.system(pr.grid, pr.material, pr.loads)
+        u = fem.solve(Abc, f)
+        e_l2, e_en = fem.manufactured_errors(pr.grid, pr.material, u)
+        l2.append(e_l2)
+        en.append(e_en)
+        hs.append(1.0 / (pr.grid.n - 1))
+    s_l2 = np.polyfit(np.log(hs), np.log(l2), 1)[0]
+    s_en = np.polyfit(np.log(hs), np.log(en), 1)[0]
+    assert abs(s_l2 - 2.0) < 0.2, s_l2
+    assert abs(s_en - 1.0) < 0.2, s_en
+
+
+def test_dense_direct_solve_agrees_and_galerkin_identity():
+    pr = W.steel_plate_2d(levels=4)
+    Abc, f = fem.system(pr.grid, pr.material, pr.loads)
+    u = fem.solve(Abc, f)
+    ud = np.linalg.solve(Abc.toarray(), f)
+    assert np.linalg.norm(u - ud) <= 1e-12 * np.linalg.norm(ud)
+    # A u = f => u^T A u = f^T u
+    assert u @ (Abc @ u) == pytest.approx(f @ u, rel=1e-12)
+    # clamped unknowns solve to exactly zero
+    cn = np.tile(fem.constrained_nodes(pr.grid), 2)
+    assert np.all(u[cn] == 0.0)
+    # positive definite after boundary conditions
+    lmin = np.linalg.eigvalsh(Abc.toarray()).min()
+    assert lmin > 0
+
+
+def test_bc_shift_does_not_change_solution():
+    pr = W.steel_plate_2d(levels=3)
+    A, M = fem.assemble(pr.grid, pr.material)
+    f = fem.load_vector(pr.grid, pr.material, pr.loads, M)
+    Abc, fbc = fem.apply_bc(pr.grid, A, f)
+    u1 = fem.solve(Abc, fbc)
+    free = np.tile(~fem.constrained_nodes(pr.grid), 2).astype(float)
+    Abc2 = (Abc + 7.5 * np.diag(1 - free))
+    u2 = np.linalg.solve(np.asarray(Abc2), fbc)
+    np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-12 * np.abs(u1).max())
+
+
+def test_grid_bookkeeping_golden():
+    with open(os.path.join(GOLDEN, "section5_grid_counts.json")) as fh:
+        gold = json.load(fh)
+    for case in gold["cases"]:
+        g = W.Grid(dim=2, levels=case["d"])
+        assert g.n ** 2 == case["points"]
+        assert g.dofs == case["dofs"]
+        assert (g.n - 1) ** 2 == case["elements"]
+
+
+def test_cantilever_tip_deflection_section6():
+    """Section 6: the FE tip deflection of the 20 m x 1 m aluminium cantilever approaches the
+    beam formula 3 rho g L^4 / (2 E H^2) (Euler-Bernoulli, so only to within a few percent)."""
+    with open(os.path.join(GOLDEN, "section6_cantilever.json")) as fh:
+        c = json.load(fh)
+    ref = 3 * c["rho_kg_m3"] * c["g_m_s2"] * c["length_m"] ** 4 / (2 * c["E_pa"] * c["height_m"] ** 2)
+    assert ref == pytest.approx(0.0935, rel=2e-3)
+    defl = []
+    for L in (6, 7):
+        g = W.Grid(dim=2, levels=L, lo=(0.0, 0.0, 0.0), hi=(c["length_m"], c["height_m"], 0.0),
+                   clamped=(True, False, False, False, False, False), plane_stress=True)
+        mat = W.Material(E=(c["E_pa"], c["E_pa"]), nu=c["nu"])
+        Abc, f = fem.system(g, mat, [W.Load(kind="gravity", rho=c["rho_kg_m3"], g=c["g_m_s2"])])
+        u = fem.solve(Abc, f)
+        uy = u[g.n ** 2:].reshape(g.n, g.n)
+        defl.append(abs(uy[-1, g.n // 2]))
+    # Q1 elements are too stiff in bending on 20:1 elements; refinement approaches the formula
+    assert defl[1] > defl[0]
+    assert abs(defl[1] - ref) / ref < 0.05, (defl, ref)
