@@ -146,6 +146,21 @@ tnfem_status tnfem_build_mass(tnfem_ctx* ctx, const tnfem_grid* grid, tnfem_mpo*
 tnfem_status tnfem_build_load(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfem_material* mat,
                               const tnfem_load* loads, int n_loads, tnfem_tt** out);
 
+/* Host-only variants of the three builders above: they run the exact host construction
+ * (Kronecker sums of 1D QTT matrices, Section 5.2 / 5.3) without device rounding and without
+ * touching any GPU, and copy the train into caller memory.  Call with cores == NULL to get
+ * ncores, ranks (ncores+1 entries, caller provides >= 64) and modes (>= 63) for sizing; then
+ * again with `cores` holding sum_k ranks[k]*modes[k]*(modes[k] for operators)*ranks[k+1]
+ * doubles, laid out as in tnfem_tt_export / tnfem_mpo_export.  `shift` (nullable) receives the
+ * boundary-condition shift s of the stiffness operator. */
+tnfem_status tnfem_host_stiffness(const tnfem_grid* grid, const tnfem_material* mat, int* ncores,
+                                  int* ranks, int* modes, double* cores, double* shift);
+tnfem_status tnfem_host_mass(const tnfem_grid* grid, int* ncores, int* ranks, int* modes,
+                             double* cores);
+tnfem_status tnfem_host_load(const tnfem_grid* grid, const tnfem_material* mat,
+                             const tnfem_load* loads, int n_loads, int* ncores, int* ranks,
+                             int* modes, double* cores);
+
 /* ---- solve (Algorithm 2) ----------------------------------------------------------------- */
 
 /* Solve A u = f by AMEn (Section 5.4).  x0 may be NULL (a seeded rank-2 start is used).

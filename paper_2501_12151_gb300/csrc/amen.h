@@ -1,0 +1,43 @@
+// AMEn solve on the device (see amen.cu).
+#pragma once
+
+#include <vector>
+
+#include "internal.h"
+
+namespace tnfem {
+
+// One term of the right-hand side b = sum_s coef * S: a train v (is_op == false) or the
+// operator applied to a train, A v (is_op == true, same operator as the system).
+struct AmenSource {
+  const tnfem_tt* v = nullptr;
+  bool is_op = false;
+  double coef = 1.0;
+};
+
+struct AmenParams {
+  double tol = 1e-10;       // stop when the largest local residual or local update is <= tol
+  int rmax = 64;            // rank cap
+  int kick = 4;             // enrichment rank
+  int max_sweeps = 40;
+  int local_maxit = 500;    // conjugate-gradient iterations per local solve
+  double resid_damp = 2.0;  // local solves stop at tol / resid_damp
+  uint64_t seed = 0;
+  bool verbose = false;
+};
+
+struct AmenStats {
+  int sweeps = 0;
+  int max_rank = 0;
+  int last_rank_trunc = 0;
+  long long local_iters = 0;
+  double max_res = 0, max_dx = 0;
+  double flops = 0;
+  bool converged = false;
+};
+
+// Solve A x = b; `single` selects binary32 for the sweep (sources stay binary64).
+tnfem_tt* amen_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const std::vector<AmenSource>& src,
+                     const AmenParams& prm, const tnfem_tt* x0, bool single, AmenStats& st);
+
+}  // namespace tnfem

@@ -1,0 +1,224 @@
+// Internal declarations of the tnfem library: context, device buffers, tensor trains and the
+// kernel launchers shared by the host drivers.  Not part of the public ABI (include/tnfem.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "tnfem.h"
+
+namespace tnfem {
+
+// ---- errors ----------------------------------------------------------------------------------
+
+struct Error : public std::runtime_error {
+  tnfem_status status;
+  Error(tnfem_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define TN_CHECK_CUDA(call)                                                                   \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      throw ::tnfem::Error(TNFEM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+#define TN_REQUIRE(cond, msg)                                             \
+  do {                                                                    \
+    if (!(cond)) throw ::tnfem::Error(TNFEM_E_INVALID, std::string(msg)); \
+  } while (0)
+
+}  // namespace tnfem
+
+// ---- context ---------------------------------------------------------------------------------
+
+struct tnfem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  tnfem_alloc_fn alloc_fn = nullptr;
+  tnfem_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  std::string err;
+  long long launches = 0;
+  // per-context scratch for reductions and small device scalars
+  double* scratch = nullptr;  // kScratchDoubles doubles
+  // pinned host staging for small device->host reads
+  double* host_pinned = nullptr;
+};
+
+namespace tnfem {
+
+constexpr int kScratchDoubles = 1 << 16;
+constexpr int kReduceBlocks = 304;  // 2 x 152 SMs: partial sums of one reduction
+
+void* dalloc(tnfem_ctx* ctx, size_t bytes);
+void dfree(tnfem_ctx* ctx, void* p);
+void sync(tnfem_ctx* ctx);
+inline void count_launch(tnfem_ctx* ctx, int n = 1) { ctx->launches += n; }
+void check_launch(tnfem_ctx* ctx, const char* what);
+
+// RAII device array
+template <typename T>
+struct DArr {
+  tnfem_ctx* ctx = nullptr;
+  T* p = nullptr;
+  size_t n = 0;
+  DArr() = default;
+  DArr(tnfem_ctx* c, size_t count) : ctx(c), n(count) {
+    p = count ? static_cast<T*>(dalloc(c, count * sizeof(T))) : nullptr;
+  }
+  DArr(const DArr&) = delete;
+  DArr& operator=(const DArr&) = delete;
+  DArr(DArr&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DArr& operator=(DArr&& o) noexcept {
+    if (this != &o) { release(); ctx = o.ctx; p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DArr() { release(); }
+  void release() { if (p) dfree(ctx, p); p = nullptr; n = 0; }
+  void ensure(tnfem_ctx* c, size_t count) {
+    if (count > n) { release(); ctx = c; p = static_cast<T*>(dalloc(c, count * sizeof(T))); n = count; }
+  }
+};
+
+// ---- kernel launchers (kernels_blas.cu) ------------------------------------------------------
+
+// Strided batched GEMM: C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n) for each batch b,
+// A(m,k) = A[b*sAb + m*sAm + k*sAk], B(k,n) = B[b*sBb + k*sBk + n*sBn],
+// C(m,n) = C[b*sCb + m*sCm + n*sCn].  `work` (nullable) enables split-K through a deterministic
+// two-pass reduction; it must hold splits*batch*M*N elements.
+struct GemmDesc {
+  int M, N, K, batch;
+  long long sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb;
+};
+template <typename T>
+void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T beta, T* C,
+          T* work = nullptr, size_t work_elems = 0, const int* skip = nullptr);
+
+template <typename T> void fill(tnfem_ctx* ctx, T* x, T v, size_t n);
+template <typename T> void copy(tnfem_ctx* ctx, T* dst, const T* src, size_t n);
+template <typename T> void axpby(tnfem_ctx* ctx, T* y, T a, const T* x, T b, size_t n);  // y = a x + b y
+template <typename T> void scale(tnfem_ctx* ctx, T* x, T a, size_t n);
+void convert_d2f(tnfem_ctx* ctx, float* dst, const double* src, size_t n);
+void convert_f2d(tnfem_ctx* ctx, double* dst, const float* src, size_t n);
+// Partial sums of x.y into part[0..kReduceBlocks) (deterministic order).
+template <typename T> void dot_partials(tnfem_ctx* ctx, const T* x, const T* y, size_t n, double* part);
+// Host-side dot / norm (synchronising).
+template <typename T> double dot(tnfem_ctx* ctx, const T* x, const T* y, size_t n);
+template <typename T> double nrm2(tnfem_ctx* ctx, const T* x, size_t n);
+// out[c][b][a] = in[a][b][c] for a [A][B][C] array (used to flip tensor-train cores)
+template <typename T> void transpose3(tnfem_ctx* ctx, T* out, const T* in, int A, int B, int C);
+// out[d][b][c][a] = in[a][b][c][d] (flip operator cores)
+template <typename T> void transpose4_outer(tnfem_ctx* ctx, T* out, const T* in, int A, int B, int C, int D);
+// out[a][j][i][d] = in[a][i][j][d] (swap the two middle indices)
+template <typename T> void transpose4_mid(tnfem_ctx* ctx, T* out, const T* in, int A, int B, int C, int D);
+// 2D transpose: out[n][m] = in[m][n]
+template <typename T> void transpose2(tnfem_ctx* ctx, T* out, const T* in, int m, int n);
+
+// ---- dense factorizations (kernels_la.cu) ----------------------------------------------------
+
+// Reduced Householder QR of row-major m x n matrix A (overwritten as workspace):
+// Q [m][k], R [k][n], k = min(m, n).
+template <typename T>
+void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work);
+size_t qr_work_elems(int m, int n);
+// Thin SVD by one-sided Jacobi of row-major m x n matrix (m >= n), A overwritten:
+// U [m][n] (unit columns, sign fixed), S [n] descending, Vt [n][n].
+template <typename T>
+void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work);
+size_t svd_work_elems(int m, int n);
+
+}  // namespace tnfem
+
+// ---- tensor trains ---------------------------------------------------------------------------
+
+struct tnfem_tt {
+  tnfem_ctx* ctx = nullptr;
+  int d = 0;
+  std::vector<int> n;       // modes, size d
+  std::vector<int> r;       // ranks, size d+1
+  std::vector<double*> core;
+  std::vector<size_t> cap;  // capacity (elements) of each core
+  ~tnfem_tt();
+};
+
+struct tnfem_mpo {
+  tnfem_ctx* ctx = nullptr;
+  int d = 0;
+  std::vector<int> n;       // modes
+  std::vector<int> a;       // ranks, size d+1
+  std::vector<double*> core;        // [a0][n][n][a1]
+  // Derived copies used by the sweep (built by mpo_prepare): cores with the two mode indices
+  // swapped, [a0][j][i][a1], in the given and in the flipped orientation (cores reversed,
+  // [a1][j][i][a0]), in binary64 and binary32.
+  std::vector<double*> p64[2];
+  std::vector<float*> p32[2];
+  bool prepared = false;
+  ~tnfem_mpo();
+};
+
+namespace tnfem {
+
+tnfem_tt* tt_new(tnfem_ctx* ctx, const std::vector<int>& n, const std::vector<int>& r,
+                 const std::vector<size_t>* cap = nullptr);
+void tt_set_core(tnfem_tt* x, int k, int r0, int r1);  // change rank, keep buffer if it fits
+tnfem_tt* tt_clone(const tnfem_tt* x);
+tnfem_mpo* mpo_new(tnfem_ctx* ctx, const std::vector<int>& n, const std::vector<int>& a);
+void mpo_prepare(tnfem_mpo* A);
+// random Gaussian core entries from a counter-based generator (splitmix64 + Box-Muller)
+void fill_gaussian(tnfem_ctx* ctx, double* x, size_t n, uint64_t seed, uint64_t stream_id);
+// dst[(off0+a)][i][(off1+b)] = s * src[a][i][b] inside a [R0][n][R1] array
+void block_copy3(tnfem_ctx* ctx, double* dst, int R0, int n, int R1, int off0, int off1,
+                 const double* src, int r0, int r1, double s);
+// dst[i][c] = src[i*ld + c] * s[c], c < ncols (s is a device array)
+void scale_cols(tnfem_ctx* ctx, double* dst, const double* src, int rows, int ld, int ncols,
+                const double* s);
+int truncation_rank(const std::vector<double>& S, double delta, int rmax);
+size_t tt_bytes(const tnfem_tt* x);
+size_t mpo_bytes(const tnfem_mpo* A);
+
+// TT algebra on the device (tt_ops.cu)
+tnfem_tt* tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax);
+tnfem_tt* tt_axpy(tnfem_ctx* ctx, const tnfem_tt* x, double beta, const tnfem_tt* y);
+tnfem_tt* mpo_apply(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* x);
+double tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y);
+double tt_norm(tnfem_ctx* ctx, const tnfem_tt* x);
+double energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u, const tnfem_tt* v);
+// MPO rounding (as a train with mode n^2)
+tnfem_mpo* mpo_round(tnfem_ctx* ctx, const tnfem_mpo* A, double eps, int rmax);
+
+// Contractions shared by the sweep and the entry points (contract.cu)
+template <typename T>
+struct Workspace;
+// y = local matvec; T1/T2 workspaces sized by local_ws_elems
+size_t local_ws_elems(int r0, int n, int r1, int a0, int a1);
+template <typename T>
+void local_matvec(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1, const T* PhiL,
+                  const T* A, const T* PhiR, const T* x, T* y, T* ws, size_t ws_elems,
+                  const int* skip = nullptr);
+// Left environment update, operator: out[b',g,b] = sum y[a',i,b'] Phi[a',beta,a] A[beta,i,j,g] x[a,j,b]
+template <typename T>
+void env_left(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx1, int n, int a0, int a1,
+              const T* Phi, const T* y, const T* A, const T* x, T* out, T* ws, size_t ws_elems);
+// Left environment update, vector: out[b',d] = sum y[a',i,b'] Psi[a',c] f[c,i,d]
+template <typename T>
+void env_left_vec(tnfem_ctx* ctx, int ry0, int ry1, int rf0, int rf1, int n, const T* Psi,
+                  const T* y, const T* f, T* out, T* ws, size_t ws_elems);
+// Local right-hand side g = alpha * (sum PsiL[a',c] f[c,i,d] PsiR[b',d]) + beta * g
+template <typename T>
+void local_rhs(tnfem_ctx* ctx, int r0, int n, int r1, int rf0, int rf1, const T* PsiL,
+               const T* f, const T* PsiR, T* g, T* ws, size_t ws_elems, T alpha = T(1),
+               T beta = T(0));
+// Rectangular local operator application with separate bra (ry) and ket (rx) ranks:
+// y[a',i,b'] = alpha * sum PhiL[a',beta,a] A[beta,i,j,g] PhiR[b',g,b] x[a,j,b] + beta_ * y
+template <typename T>
+void local_apply(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx1, int n, int a0, int a1,
+                 const T* PhiL, const T* Ap, const T* PhiR, const T* x, T* y, T alpha, T beta,
+                 T* ws, size_t ws_elems, const int* skip = nullptr);
+
+}  // namespace tnfem

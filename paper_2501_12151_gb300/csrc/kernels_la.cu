@@ -1,0 +1,258 @@
+// Dense factorizations used by the sweep's orthogonalisation and truncation steps:
+// Householder QR (the reduced QR of Section 4, Eq. qr) and the one-sided Jacobi (Hestenes)
+// SVD used for TT truncation.  One CTA of 1024 threads works on a matrix held in global
+// memory (L2/L1-resident at these sizes); all loops have fixed trip counts, nothing waits on
+// another block.
+#include <cfloat>
+
+#include "internal.h"
+
+namespace tnfem {
+
+namespace {
+
+constexpr int LT = 1024;
+
+template <typename T> __device__ __forceinline__ T eps_of();
+template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sh[l] : T(0);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (l == 0) sh[32] = v;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// A: m x n row-major, overwritten by the Householder vectors (below the diagonal) and R.
+// tau: k scalars.  Q: m x k row-major (explicit), R: k x n row-major.
+template <typename T>
+__global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A, T* __restrict__ Q,
+                                                T* __restrict__ R, T* __restrict__ tau) {
+  __shared__ T sh[33];
+  __shared__ T s_beta, s_tau, s_v0;
+  const int k = min(m, n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    T part = T(0);
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+      T v = A[(long long)i * n + j];
+      part += v * v;
+    }
+    T tail = block_sum(part, sh);
+    if (threadIdx.x == 0) {
+      T alpha = A[(long long)j * n + j];
+      if (tail == T(0)) {
+        s_tau = T(0);
+        s_beta = alpha;
+        s_v0 = T(1);
+      } else {
+        T nx = sqrt(alpha * alpha + tail);
+        T beta = alpha >= T(0) ? -nx : nx;
+        s_tau = (beta - alpha) / beta;
+        s_v0 = alpha - beta;
+        s_beta = beta;
+      }
+      tau[j] = s_tau;
+    }
+    __syncthreads();
+    const T tj = s_tau, v0 = s_v0;
+    // scale the vector: v = [1, x_{j+1..}/v0]
+    if (tj != T(0)) {
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(long long)i * n + j] /= v0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[(long long)j * n + j] = s_beta;
+    // apply H = I - tau v v^T to trailing columns, one warp per column
+    if (tj != T(0)) {
+      for (int c = j + 1 + warp; c < n; c += nw) {
+        T w = T(0);
+        for (int i = j + lane; i < m; i += 32) {
+          T vi = (i == j) ? T(1) : A[(long long)i * n + j];
+          w += vi * A[(long long)i * n + c];
+        }
+        w = warp_sum(w) * tj;
+        for (int i = j + lane; i < m; i += 32) {
+          T vi = (i == j) ? T(1) : A[(long long)i * n + j];
+          A[(long long)i * n + c] -= w * vi;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // R = upper triangle of the first k rows
+  for (long long t = threadIdx.x; t < (long long)k * n; t += blockDim.x) {
+    int i = (int)(t / n), c = (int)(t % n);
+    R[t] = (c >= i) ? A[(long long)i * n + c] : T(0);
+  }
+  // Q = H_0 ... H_{k-1} [I_k; 0]
+  for (long long t = threadIdx.x; t < (long long)m * k; t += blockDim.x) {
+    int i = (int)(t / k), c = (int)(t % k);
+    Q[t] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj == T(0)) continue;
+    for (int c = j + warp; c < k; c += nw) {
+      T w = T(0);
+      for (int i = j + lane; i < m; i += 32) {
+        T vi = (i == j) ? T(1) : A[(long long)i * n + j];
+        w += vi * Q[(long long)i * k + c];
+      }
+      w = warp_sum(w) * tj;
+      for (int i = j + lane; i < m; i += 32) {
+        T vi = (i == j) ? T(1) : A[(long long)i * n + j];
+        Q[(long long)i * k + c] -= w * vi;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided Jacobi SVD.  G: m x n column-major work copy of A, V: n x n column-major.
+template <typename T>
+__global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
+                                                 T* __restrict__ S, T* __restrict__ Vt,
+                                                 T* __restrict__ G, T* __restrict__ V,
+                                                 T* __restrict__ sig, int max_sweeps) {
+  __shared__ int s_rot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long t = threadIdx.x; t < (long long)m * n; t += blockDim.x) {
+    int i = (int)(t / n), j = (int)(t % n);
+    G[(long long)j * m + i] = A[t];
+  }
+  for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    V[t] = (i == j) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const int np = n + (n & 1);  // players, with a dummy when n is odd
+  const T tol = eps_of<T>() * (T)4;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int pi = warp; pi < np / 2; pi += nw) {
+        int p, q;
+        if (pi == 0) { p = r; q = np - 1; }
+        else { p = (r + pi) % (np - 1); q = (r - pi + (np - 1)) % (np - 1); }
+        if (p >= n || q >= n) continue;
+        if (p > q) { int t = p; p = q; q = t; }
+        T* gp = G + (long long)p * m;
+        T* gq = G + (long long)q * m;
+        T a = T(0), b = T(0), c = T(0);
+        for (int i = lane; i < m; i += 32) {
+          T x = gp[i], y = gq[i];
+          a += x * x; b += y * y; c += x * y;
+        }
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (c == T(0) || a == T(0) || b == T(0)) continue;
+        if (fabs(c) <= tol * sqrt(a * b)) continue;
+        T zeta = (b - a) / (T(2) * c);
+        T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        T cs = T(1) / sqrt(T(1) + t * t);
+        T sn = cs * t;
+        for (int i = lane; i < m; i += 32) {
+          T x = gp[i], y = gq[i];
+          gp[i] = cs * x - sn * y;
+          gq[i] = sn * x + cs * y;
+        }
+        T* vp = V + (long long)p * n;
+        T* vq = V + (long long)q * n;
+        for (int i = lane; i < n; i += 32) {
+          T x = vp[i], y = vq[i];
+          vp[i] = cs * x - sn * y;
+          vq[i] = sn * x + cs * y;
+        }
+        if (lane == 0) atomicAdd(&s_rot, 1);
+      }
+      __syncthreads();
+    }
+    int rot = s_rot;
+    __syncthreads();
+    if (rot == 0) break;
+  }
+  // singular values
+  for (int j = warp; j < n; j += nw) {
+    T s = T(0);
+    for (int i = lane; i < m; i += 32) s += G[(long long)j * m + i] * G[(long long)j * m + i];
+    s = warp_sum(s);
+    if (lane == 0) sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  // order: rank by descending value, ties by index
+  for (int j = warp; j < n; j += nw) {
+    const T sj = sig[j];
+    int pos = 0;
+    for (int i = lane; i < n; i += 32) {
+      T si = sig[i];
+      pos += (si > sj || (si == sj && i < j)) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+    // sign: make the entry of largest magnitude of u_j positive
+    T best = T(-1);
+    int bi = 0;
+    for (int i = lane; i < m; i += 32) {
+      T v = fabs(G[(long long)j * m + i]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    T sgn = (G[(long long)j * m + bi] < T(0)) ? T(-1) : T(1);
+    T inv = sj > T(0) ? sgn / sj : T(0);
+    for (int i = lane; i < m; i += 32) U[(long long)i * n + pos] = G[(long long)j * m + i] * inv;
+    for (int i = lane; i < n; i += 32) Vt[(long long)pos * n + i] = sgn * V[(long long)j * n + i];
+    if (lane == 0) S[pos] = sj;
+  }
+}
+
+}  // namespace
+
+size_t qr_work_elems(int m, int n) { return (size_t)std::min(m, n) + 8; }
+size_t svd_work_elems(int m, int n) { return (size_t)m * n + (size_t)n * n + (size_t)n + 8; }
+
+template <typename T>
+void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
+  if (m <= 0 || n <= 0) return;
+  qr_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, Q, R, work);
+  count_launch(ctx);
+  check_launch(ctx, "qr");
+}
+
+template <typename T>
+void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
+  if (m <= 0 || n <= 0) return;
+  TN_REQUIRE(m >= n, "svd: needs m >= n");
+  T* G = work;
+  T* V = G + (size_t)m * n;
+  T* sig = V + (size_t)n * n;
+  svd_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, U, S, Vt, G, V, sig, sizeof(T) == 8 ? 60 : 40);
+  count_launch(ctx);
+  check_launch(ctx, "svd");
+}
+
+template void qr<double>(tnfem_ctx*, int, int, double*, double*, double*, double*);
+template void qr<float>(tnfem_ctx*, int, int, float*, float*, float*, float*);
+template void svd<double>(tnfem_ctx*, int, int, double*, double*, double*, double*, double*);
+template void svd<float>(tnfem_ctx*, int, int, float*, float*, float*, float*, float*);
+
+}  // namespace tnfem

@@ -1,0 +1,496 @@
+// Tensor-train data structures and TT algebra on the device: rounding (left-to-right
+// Householder QR, then right-to-left truncated SVD, Section 4 Eq. qr), exact sums and
+// operator-times-train products, inner products, norms and the energy norm of a difference.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+using namespace tnfem;
+
+tnfem_tt::~tnfem_tt() {
+  for (double* p : core)
+    if (p) dfree(ctx, p);
+}
+
+tnfem_mpo::~tnfem_mpo() {
+  for (double* p : core)
+    if (p) dfree(ctx, p);
+  for (int o = 0; o < 2; ++o) {
+    for (double* p : p64[o])
+      if (p) dfree(ctx, p);
+    for (float* p : p32[o])
+      if (p) dfree(ctx, p);
+  }
+}
+
+namespace tnfem {
+
+void* dalloc(tnfem_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (ctx->alloc_fn) {
+    p = ctx->alloc_fn(bytes, ctx->user);
+    if (!p) throw Error(TNFEM_E_NOMEM, "device allocation callback failed for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(TNFEM_E_NOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  return p;
+}
+
+void dfree(tnfem_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->free_fn) ctx->free_fn(p, ctx->user);
+  else cudaFree(p);
+}
+
+void sync(tnfem_ctx* ctx) { TN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream)); }
+
+tnfem_tt* tt_new(tnfem_ctx* ctx, const std::vector<int>& n, const std::vector<int>& r,
+                 const std::vector<size_t>* cap) {
+  auto* x = new tnfem_tt();
+  x->ctx = ctx;
+  x->d = (int)n.size();
+  x->n = n;
+  x->r = r;
+  x->core.assign(x->d, nullptr);
+  x->cap.assign(x->d, 0);
+  try {
+    for (int k = 0; k < x->d; ++k) {
+      size_t need = (size_t)r[k] * n[k] * r[k + 1];
+      size_t c = cap ? std::max(need, (*cap)[k]) : need;
+      x->core[k] = static_cast<double*>(dalloc(ctx, c * sizeof(double)));
+      x->cap[k] = c;
+    }
+  } catch (...) {
+    delete x;
+    throw;
+  }
+  return x;
+}
+
+void tt_set_core(tnfem_tt* x, int k, int r0, int r1) {
+  size_t need = (size_t)r0 * x->n[k] * r1;
+  if (need > x->cap[k]) {
+    double* p = static_cast<double*>(dalloc(x->ctx, need * sizeof(double)));
+    dfree(x->ctx, x->core[k]);
+    x->core[k] = p;
+    x->cap[k] = need;
+  }
+  x->r[k] = r0;
+  x->r[k + 1] = r1;
+}
+
+tnfem_tt* tt_clone(const tnfem_tt* x) {
+  tnfem_tt* y = tt_new(x->ctx, x->n, x->r);
+  for (int k = 0; k < x->d; ++k)
+    copy<double>(x->ctx, y->core[k], x->core[k], (size_t)x->r[k] * x->n[k] * x->r[k + 1]);
+  return y;
+}
+
+tnfem_mpo* mpo_new(tnfem_ctx* ctx, const std::vector<int>& n, const std::vector<int>& a) {
+  auto* A = new tnfem_mpo();
+  A->ctx = ctx;
+  A->d = (int)n.size();
+  A->n = n;
+  A->a = a;
+  A->core.assign(A->d, nullptr);
+  try {
+    for (int k = 0; k < A->d; ++k)
+      A->core[k] = static_cast<double*>(dalloc(ctx, (size_t)a[k] * n[k] * n[k] * a[k + 1] * sizeof(double)));
+  } catch (...) {
+    delete A;
+    throw;
+  }
+  return A;
+}
+
+void mpo_prepare(tnfem_mpo* A) {
+  if (A->prepared) return;
+  tnfem_ctx* ctx = A->ctx;
+  const int d = A->d;
+  for (int o = 0; o < 2; ++o) {
+    A->p64[o].assign(d, nullptr);
+    A->p32[o].assign(d, nullptr);
+  }
+  size_t maxc = 0;
+  for (int k = 0; k < d; ++k) maxc = std::max(maxc, (size_t)A->a[k] * A->n[k] * A->n[k] * A->a[k + 1]);
+  DArr<double> tmp(ctx, maxc);
+  for (int k = 0; k < d; ++k) {
+    const int a0 = A->a[k], n = A->n[k], a1 = A->a[k + 1];
+    const size_t sz = (size_t)a0 * n * n * a1;
+    // given orientation: [a0][j][i][a1]
+    A->p64[0][k] = static_cast<double*>(dalloc(ctx, sz * sizeof(double)));
+    transpose4_mid<double>(ctx, A->p64[0][k], A->core[k], a0, n, n, a1);
+    // flipped orientation: core d-1-k of the flipped train is [a1][n][n][a0]; swap its modes too
+    const int kf = d - 1 - k;
+    A->p64[1][kf] = static_cast<double*>(dalloc(ctx, sz * sizeof(double)));
+    transpose4_outer<double>(ctx, tmp.p, A->core[k], a0, n, n, a1);  // [a1][i][j][a0]
+    transpose4_mid<double>(ctx, A->p64[1][kf], tmp.p, a1, n, n, a0);  // [a1][j][i][a0]
+    for (int o = 0; o < 2; ++o) {
+      int kk = o == 0 ? k : kf;
+      A->p32[o][kk] = static_cast<float*>(dalloc(ctx, sz * sizeof(float)));
+      convert_d2f(ctx, A->p32[o][kk], A->p64[o][kk], sz);
+    }
+    sync(ctx);
+  }
+  A->prepared = true;
+}
+
+size_t tt_bytes(const tnfem_tt* x) {
+  size_t s = 0;
+  for (int k = 0; k < x->d; ++k) s += (size_t)x->r[k] * x->n[k] * x->r[k + 1] * sizeof(double);
+  return s;
+}
+
+size_t mpo_bytes(const tnfem_mpo* A) {
+  size_t s = 0;
+  for (int k = 0; k < A->d; ++k) s += (size_t)A->a[k] * A->n[k] * A->n[k] * A->a[k + 1] * sizeof(double);
+  return s;
+}
+
+// ---- random cores ------------------------------------------------------------------------------
+
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(double* x, size_t n, uint64_t seed, uint64_t sid) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint64_t key = splitmix64(seed ^ splitmix64(sid * 0x100000001B3ull + i));
+    uint64_t a = splitmix64(key), b = splitmix64(key ^ 0xD1B54A32D192ED03ull);
+    // uniform in (0, 1]: 53 random bits
+    double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+    double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    x[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+__global__ void block_copy3_kernel(double* __restrict__ dst, int R0, int n, int R1, int off0, int off1,
+                                   const double* __restrict__ src, int r0, int r1, double s) {
+  long long total = (long long)r0 * n * r1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(t % r1);
+    long long q = t / r1;
+    int i = (int)(q % n);
+    int a = (int)(q / n);
+    dst[((long long)(off0 + a) * n + i) * R1 + off1 + b] = s * src[t];
+  }
+}
+
+// out[(beta a)][i][(g b)] = sum_j A[beta][i][j][g] x[a][j][b]
+__global__ void mpo_apply_kernel(double* __restrict__ out, const double* __restrict__ A,
+                                 const double* __restrict__ x, int a0, int n, int a1, int r0, int r1) {
+  long long total = (long long)a0 * r0 * n * a1 * r1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(t % r1);
+    long long q = t / r1;
+    int g = (int)(q % a1);
+    q /= a1;
+    int i = (int)(q % n);
+    q /= n;
+    int a = (int)(q % r0);
+    int be = (int)(q / r0);
+    double s = 0.0;
+    const double* Ar = A + (((long long)be * n + i) * n) * a1 + g;
+    const double* xr = x + (long long)a * n * r1 + b;
+    for (int j = 0; j < n; ++j) s += Ar[(long long)j * a1] * xr[(long long)j * r1];
+    out[t] = s;
+  }
+}
+
+// dst[i][c] = src[i*ld + c] * s[c] for c < ncols
+__global__ void scale_cols_kernel(double* __restrict__ dst, const double* __restrict__ src, int rows,
+                                  int ld, int ncols, const double* __restrict__ s) {
+  long long total = (long long)rows * ncols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t / ncols), c = (int)(t % ncols);
+    dst[t] = src[(long long)i * ld + c] * s[c];
+  }
+}
+
+inline int gblocks(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 16)); }
+
+}  // namespace
+
+void fill_gaussian(tnfem_ctx* ctx, double* x, size_t n, uint64_t seed, uint64_t sid) {
+  if (!n) return;
+  gaussian_kernel<<<gblocks((long long)n), 256, 0, ctx->stream>>>(x, n, seed, sid);
+  count_launch(ctx);
+  check_launch(ctx, "gaussian");
+}
+
+void block_copy3(tnfem_ctx* ctx, double* dst, int R0, int n, int R1, int off0, int off1, const double* src,
+                 int r0, int r1, double s) {
+  long long total = (long long)r0 * n * r1;
+  if (!total) return;
+  block_copy3_kernel<<<gblocks(total), 256, 0, ctx->stream>>>(dst, R0, n, R1, off0, off1, src, r0, r1, s);
+  count_launch(ctx);
+  check_launch(ctx, "block_copy3");
+}
+
+void scale_cols(tnfem_ctx* ctx, double* dst, const double* src, int rows, int ld, int ncols, const double* s) {
+  if ((long long)rows * ncols == 0) return;
+  scale_cols_kernel<<<gblocks((long long)rows * ncols), 256, 0, ctx->stream>>>(dst, src, rows, ld, ncols, s);
+  count_launch(ctx);
+  check_launch(ctx, "scale_cols");
+}
+
+// Truncation rank: smallest r whose discarded tail sum_{i>=r} s_i^2 <= delta^2, capped.
+int truncation_rank(const std::vector<double>& S, double delta, int rmax) {
+  int n = (int)S.size();
+  std::vector<double> tail(n + 1, 0.0);
+  for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + S[i] * S[i];
+  int r = n;
+  for (int i = 0; i < n; ++i) {
+    if (std::sqrt(tail[i]) <= delta) { r = i; break; }
+  }
+  r = std::max(1, std::min(r, rmax));
+  return r;
+}
+
+// ---- rounding --------------------------------------------------------------------------------
+
+// Left-orthogonalise cores 0..d-2 of y in place (y has room for the ranks it gets).
+static void orthogonalize_left_inplace(tnfem_ctx* ctx, tnfem_tt* y) {
+  const int d = y->d;
+  size_t maxw = 0;
+  for (int k = 0; k < d; ++k) maxw = std::max(maxw, (size_t)y->r[k] * y->n[k] * y->r[k + 1]);
+  DArr<double> A(ctx, maxw), Q(ctx, maxw), R(ctx, maxw + 64), tmp(ctx, maxw), qw(ctx, 4096 + maxw / 16);
+  for (int k = 0; k < d - 1; ++k) {
+    const int r0 = y->r[k], n = y->n[k], r1 = y->r[k + 1];
+    const int m = r0 * n, kk = std::min(m, r1);
+    copy<double>(ctx, A.p, y->core[k], (size_t)m * r1);
+    qw.ensure(ctx, qr_work_elems(m, r1));
+    qr<double>(ctx, m, r1, A.p, Q.p, R.p, qw.p);
+    // next core <- R * next   (kk x r1) (r1 x n2 r2)
+    const int n2 = y->n[k + 1], r2 = y->r[k + 2];
+    GemmDesc g{kk, n2 * r2, r1, 1, r1, 1, 0, (long long)n2 * r2, 1, 0, (long long)n2 * r2, 1, 0};
+    tmp.ensure(ctx, (size_t)kk * n2 * r2);
+    gemm<double>(ctx, g, 1.0, R.p, y->core[k + 1], 0.0, tmp.p);
+    tt_set_core(y, k, r0, kk);
+    copy<double>(ctx, y->core[k], Q.p, (size_t)m * kk);
+    tt_set_core(y, k + 1, kk, r2);
+    copy<double>(ctx, y->core[k + 1], tmp.p, (size_t)kk * n2 * r2);
+  }
+  sync(ctx);
+}
+
+tnfem_tt* tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax) {
+  const int d = x->d;
+  tnfem_tt* y = tt_clone(x);
+  try {
+    if (d == 1) return y;
+    orthogonalize_left_inplace(ctx, y);
+    const double nrm = nrm2<double>(ctx, y->core[d - 1], (size_t)y->r[d - 1] * y->n[d - 1] * y->r[d]);
+    const double delta = eps / std::sqrt((double)(d - 1)) * nrm;
+    std::vector<double> S;
+    for (int k = d - 1; k >= 1; --k) {
+      const int r0 = y->r[k], n = y->n[k], r1 = y->r[k + 1];
+      const int w = n * r1;  // M = core as r0 x w
+      const int p = std::min(r0, w);
+      DArr<double> Mt(ctx, (size_t)r0 * w), U(ctx, (size_t)std::max(r0, w) * p), Sd(ctx, p + 8),
+          Vt(ctx, (size_t)p * p), sw(ctx, svd_work_elems(std::max(r0, w), p));
+      DArr<double> left(ctx, (size_t)r0 * p), right(ctx, (size_t)p * w);
+      if (w >= r0) {
+        // M^T (w x r0) = U S Vt  =>  M = Vt^T S U^T: new core = U^T (rows), left factor Vt^T S
+        transpose2<double>(ctx, Mt.p, y->core[k], r0, w);
+        svd<double>(ctx, w, r0, Mt.p, U.p, Sd.p, Vt.p, sw.p);
+        transpose2<double>(ctx, right.p, U.p, w, p);     // p x w
+        transpose2<double>(ctx, left.p, Vt.p, p, p);     // r0 x p (= Vt^T)
+      } else {
+        // M (r0 x w), r0 > w: M = U S Vt: new core = Vt, left factor U S
+        copy<double>(ctx, Mt.p, y->core[k], (size_t)r0 * w);
+        svd<double>(ctx, r0, w, Mt.p, U.p, Sd.p, Vt.p, sw.p);
+        copy<double>(ctx, right.p, Vt.p, (size_t)p * w);
+        copy<double>(ctx, left.p, U.p, (size_t)r0 * p);
+      }
+      S.assign(p, 0.0);
+      TN_CHECK_CUDA(cudaMemcpyAsync(S.data(), Sd.p, p * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+      const int rk = truncation_rank(S, delta, rmax);
+      // LS = left[:, :rk] * diag(S[:rk])  (r0 x rk), applied to the previous core
+      DArr<double> LS(ctx, (size_t)r0 * rk);
+      scale_cols(ctx, LS.p, left.p, r0, p, rk, Sd.p);
+      const int r_prev = y->r[k - 1], n_prev = y->n[k - 1];
+      DArr<double> nc(ctx, (size_t)r_prev * n_prev * rk);
+      GemmDesc g2{r_prev * n_prev, rk, r0, 1, r0, 1, 0, rk, 1, 0, rk, 1, 0};
+      gemm<double>(ctx, g2, 1.0, y->core[k - 1], LS.p, 0.0, nc.p);
+      // new core k = right[:rk] (rk x w)
+      tt_set_core(y, k, rk, r1);
+      copy<double>(ctx, y->core[k], right.p, (size_t)rk * w);
+      tt_set_core(y, k - 1, r_prev, rk);
+      copy<double>(ctx, y->core[k - 1], nc.p, (size_t)r_prev * n_prev * rk);
+      sync(ctx);
+    }
+  } catch (...) {
+    delete y;
+    throw;
+  }
+  return y;
+}
+
+tnfem_mpo* mpo_round(tnfem_ctx* ctx, const tnfem_mpo* A, double eps, int rmax) {
+  std::vector<int> nn(A->d);
+  for (int k = 0; k < A->d; ++k) nn[k] = A->n[k] * A->n[k];
+  tnfem_tt* x = tt_new(ctx, nn, A->a);
+  tnfem_tt* y = nullptr;
+  tnfem_mpo* B = nullptr;
+  try {
+    for (int k = 0; k < A->d; ++k)
+      copy<double>(ctx, x->core[k], A->core[k], (size_t)A->a[k] * nn[k] * A->a[k + 1]);
+    y = tt_round(ctx, x, eps, rmax);
+    B = mpo_new(ctx, A->n, y->r);
+    for (int k = 0; k < A->d; ++k)
+      copy<double>(ctx, B->core[k], y->core[k], (size_t)y->r[k] * nn[k] * y->r[k + 1]);
+    sync(ctx);
+  } catch (...) {
+    delete x;
+    delete y;
+    delete B;
+    throw;
+  }
+  delete x;
+  delete y;
+  return B;
+}
+
+// ---- sums, products, inner products ------------------------------------------------------------
+
+tnfem_tt* tt_axpy(tnfem_ctx* ctx, const tnfem_tt* x, double beta, const tnfem_tt* y) {
+  TN_REQUIRE(x->d == y->d, "tt_axpy: different number of cores");
+  for (int k = 0; k < x->d; ++k) TN_REQUIRE(x->n[k] == y->n[k], "tt_axpy: mode mismatch");
+  const int d = x->d;
+  std::vector<int> r(d + 1);
+  r[0] = 1;
+  r[d] = 1;
+  for (int k = 1; k < d; ++k) r[k] = x->r[k] + y->r[k];
+  if (d == 1) r[1] = 1;
+  tnfem_tt* z = tt_new(ctx, x->n, r);
+  try {
+    for (int k = 0; k < d; ++k) {
+      const int n = x->n[k];
+      const size_t sz = (size_t)r[k] * n * r[k + 1];
+      if (d == 1) {
+        copy<double>(ctx, z->core[0], x->core[0], sz);
+        axpby<double>(ctx, z->core[0], beta, y->core[0], 1.0, sz);
+        continue;
+      }
+      fill<double>(ctx, z->core[k], 0.0, sz);
+      const int xo0 = 0, xo1 = 0;
+      const int yo0 = (k == 0) ? 0 : x->r[k];
+      const int yo1 = (k == d - 1) ? 0 : x->r[k + 1];
+      block_copy3(ctx, z->core[k], r[k], n, r[k + 1], xo0, xo1, x->core[k], x->r[k], x->r[k + 1], 1.0);
+      block_copy3(ctx, z->core[k], r[k], n, r[k + 1], yo0, yo1, y->core[k], y->r[k], y->r[k + 1],
+                  k == 0 ? beta : 1.0);
+    }
+    sync(ctx);
+  } catch (...) {
+    delete z;
+    throw;
+  }
+  return z;
+}
+
+tnfem_tt* mpo_apply(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* x) {
+  TN_REQUIRE(A->d == x->d, "mpo_apply: core count mismatch");
+  const int d = x->d;
+  std::vector<int> r(d + 1);
+  for (int k = 0; k <= d; ++k) r[k] = A->a[k] * x->r[k];
+  for (int k = 0; k < d; ++k) TN_REQUIRE(A->n[k] == x->n[k], "mpo_apply: mode mismatch");
+  tnfem_tt* y = tt_new(ctx, x->n, r);
+  try {
+    for (int k = 0; k < d; ++k) {
+      long long total = (long long)r[k] * x->n[k] * r[k + 1];
+      mpo_apply_kernel<<<gblocks(total), 256, 0, ctx->stream>>>(y->core[k], A->core[k], x->core[k], A->a[k],
+                                                                 x->n[k], A->a[k + 1], x->r[k], x->r[k + 1]);
+      count_launch(ctx);
+      check_launch(ctx, "mpo_apply");
+    }
+    sync(ctx);
+  } catch (...) {
+    delete y;
+    throw;
+  }
+  return y;
+}
+
+double tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y) {
+  TN_REQUIRE(x->d == y->d, "tt_dot: core count mismatch");
+  const int d = x->d;
+  size_t maxe = 1, maxw = 1;
+  for (int k = 0; k <= d; ++k) maxe = std::max(maxe, (size_t)x->r[k] * y->r[k]);
+  for (int k = 0; k < d; ++k) maxw = std::max(maxw, (size_t)x->r[k] * x->n[k] * y->r[k + 1]);
+  DArr<double> E0(ctx, maxe), E1(ctx, maxe), ws(ctx, maxw * 2 + 64 * maxe + 1024);
+  fill<double>(ctx, E0.p, 1.0, 1);
+  for (int k = 0; k < d; ++k) {
+    env_left_vec<double>(ctx, x->r[k], x->r[k + 1], y->r[k], y->r[k + 1], x->n[k], E0.p, x->core[k],
+                         y->core[k], E1.p, ws.p, ws.n);
+    std::swap(E0.p, E1.p);
+  }
+  double v = 0;
+  TN_CHECK_CUDA(cudaMemcpyAsync(&v, E0.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  return v;
+}
+
+double tt_norm(tnfem_ctx* ctx, const tnfem_tt* x) {
+  tnfem_tt* y = tt_clone(x);
+  double v = 0;
+  try {
+    orthogonalize_left_inplace(ctx, y);
+    const int d = y->d;
+    v = nrm2<double>(ctx, y->core[d - 1], (size_t)y->r[d - 1] * y->n[d - 1] * y->r[d]);
+  } catch (...) {
+    delete y;
+    throw;
+  }
+  delete y;
+  return v;
+}
+
+double energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u, const tnfem_tt* v) {
+  tnfem_tt* dlt = v ? tt_axpy(ctx, u, -1.0, v) : tt_clone(u);
+  double out = 0;
+  try {
+    // orthogonalise the difference so that its last core carries the (small) difference itself
+    orthogonalize_left_inplace(ctx, dlt);
+    mpo_prepare(const_cast<tnfem_mpo*>(A));
+    const int d = dlt->d;
+    size_t maxe = 1, maxws = 1;
+    for (int k = 0; k <= d; ++k) maxe = std::max(maxe, (size_t)dlt->r[k] * A->a[k] * dlt->r[k]);
+    for (int k = 0; k < d; ++k)
+      maxws = std::max(maxws, local_ws_elems(dlt->r[k], dlt->n[k], dlt->r[k + 1], A->a[k], A->a[k + 1]));
+    DArr<double> E0(ctx, maxe), E1(ctx, maxe), ws(ctx, maxws);
+    fill<double>(ctx, E0.p, 1.0, 1);
+    for (int k = 0; k < d; ++k) {
+      env_left<double>(ctx, dlt->r[k], dlt->r[k + 1], dlt->r[k], dlt->r[k + 1], dlt->n[k], A->a[k], A->a[k + 1],
+                       E0.p, dlt->core[k], A->p64[0][k], dlt->core[k], E1.p, ws.p, ws.n);
+      std::swap(E0.p, E1.p);
+    }
+    double q = 0;
+    TN_CHECK_CUDA(cudaMemcpyAsync(&q, E0.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    out = std::sqrt(std::max(q, 0.0));
+  } catch (...) {
+    delete dlt;
+    throw;
+  }
+  delete dlt;
+  return out;
+}
+
+}  // namespace tnfem

@@ -1,0 +1,131 @@
+"""GPU parity of the assembled operator, load and the full AMEn solve against the CPU oracle.
+
+Tolerances: the binary64 path must match the Galerkin solution u_h (oracle A: sparse element
+assembly + direct solve) to a relative energy-norm error of 1e-8 whenever the rank cap does not
+bind; with a binding cap it must be as accurate as the oracle's own AMEn (oracle B) at the same
+cap, rules and tolerance.  The mixed path (binary32 sweep inside binary64 refinement) must reach
+a relative energy-norm error of 1e-6.
+"""
+import numpy as np
+import pytest
+
+from oracle import amen, fem, mpo, tt
+from paper_2501_12151_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_12151_gb300 import tnfem
+    return tnfem.Context(0)
+
+
+def _galerkin(pr):
+    Abc, f = fem.system(pr.grid, pr.material, pr.loads)
+    return Abc, fem.solve(Abc, f)
+
+
+def _energy_err(Abc, u_qtt, uh, grid):
+    u = tt.to_natural_order(u_qtt, grid.dim, grid.levels)
+    return fem.energy_norm(Abc, u - uh) / fem.energy_norm(Abc, uh)
+
+
+@pytest.mark.parametrize("dim,levels,split", [(2, 4, 0.5), (2, 6, np.inf), (3, 2, 0.5)])
+def test_device_stiffness_matches_element_loop(ctx, dim, levels, split):
+    g = W.Grid(dim=dim, levels=levels, lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 0.5),
+               clamped=(True, False, False, dim == 2, False, False))
+    m = W.Material(E=(210e9, 70e9), nu=0.33, split_x=split)
+    A = ctx.stiffness(g, m)
+    cores = A.cores()
+    if dim * 2 ** (dim * levels) <= 8192:
+        K, _ = fem.assemble(g, m)
+        Aq = tt.matrix_to_qtt_order(fem.apply_bc(g, K), dim, levels)
+        assert np.abs(tt.mpo_full(cores) - Aq).max() <= 1e-12 * np.abs(Aq).max()
+    # the rounded operator is no larger than the oracle's rounding of the same operator
+    ref, _ = mpo.stiffness_mpo(g, m)
+    assert max(tt.ranks(cores)) <= max(tt.ranks(ref)) + 2
+
+
+def test_device_load_matches_oracle(ctx):
+    for pr in (W.manufactured_2d(levels=5), W.cantilever_3d(levels=3)):
+        f = ctx.load(pr.grid, pr.material, pr.loads).cores()
+        _, M = fem.assemble(pr.grid, pr.material)
+        ref = fem.load_vector(pr.grid, pr.material, pr.loads, M) * np.tile(~fem.constrained_nodes(pr.grid), pr.grid.dim)
+        fq = tt.to_qtt_order(ref, pr.grid.dim, pr.grid.levels)
+        np.testing.assert_allclose(tt.tt_full(f), fq, rtol=0, atol=1e-12 * np.abs(fq).max())
+
+
+@pytest.mark.parametrize("case", ["manufactured5", "steel6", "cube3"])
+def test_fp64_solve_matches_galerkin(ctx, case):
+    if case == "manufactured5":
+        pr = W.manufactured_2d(levels=5, rank_cap=64, tol=1e-11)
+    elif case == "steel6":
+        pr = W.steel_plate_2d(levels=6, rank_cap=64, tol=1e-11)
+    else:
+        pr = W.cantilever_3d(levels=3, rank_cap=64, tol=1e-11)
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    u, info = ctx.solve(A, f, pr.opts)
+    err = _energy_err(Abc, tt.tt_full(u.cores()), uh, pr.grid)
+    assert err <= 1e-8, (err, info)
+    # energy norm computed by the library agrees with the oracle's
+    ud = tt.to_natural_order(tt.tt_full(u.cores()), pr.grid.dim, pr.grid.levels)
+    assert A.energy_norm(u) == pytest.approx(fem.energy_norm(Abc, ud), rel=1e-10)
+
+
+def test_fp64_rank_capped_config_matches_oracle_amen(ctx):
+    """2D manufactured problem on 2^5 x 2^5 nodes with rank cap 16 (the cap binds): the GPU
+    solution is as close to u_h as the oracle's AMEn with the same cap and tolerance."""
+    pr = W.manufactured_2d(levels=5, rank_cap=16, tol=1e-10)
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    u, info = ctx.solve(A, f, pr.opts)
+    err_gpu = _energy_err(Abc, tt.tt_full(u.cores()), uh, pr.grid)
+    Ao, _ = mpo.stiffness_mpo(pr.grid, pr.material)
+    _, fv = fem.system(pr.grid, pr.material, pr.loads)
+    fo = mpo.load_tt_dense(fv, pr.grid)
+    x0 = W.random_tt(1, W.qtt_modes(2, 5), [1] + [2] * 5 + [1])
+    xo, _ = amen.amen_solve(Ao, fo, x0, tol=1e-10, rmax=16, nswp=40)
+    err_orc = _energy_err(Abc, tt.tt_full(xo), uh, pr.grid)
+    assert max(tt.ranks(u.cores())) <= 16 + pr.opts.kickrank
+    assert err_gpu <= 2.0 * err_orc + 1e-9, (err_gpu, err_orc)
+
+
+def test_mixed_solve_reaches_1e6(ctx):
+    pr = W.steel_plate_2d(levels=6, rank_cap=64, tol=1e-10, precision="mixed")
+    pr.opts.refine_tol = 1e-7
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    u, info = ctx.solve(A, f, pr.opts)
+    err = _energy_err(Abc, tt.tt_full(u.cores()), uh, pr.grid)
+    assert err <= 1e-6, (err, info)
+
+
+def test_displacement_and_strain_evaluation(ctx):
+    pr = W.manufactured_2d(levels=4, rank_cap=64, tol=1e-11)
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    u, _ = ctx.solve(A, f, pr.opts)
+    n = pr.grid.n
+    nodes = np.array([[0, 0], [3, 7], [15, 15], [8, 1], [15, 0]])
+    got = u.displacement(nodes)
+    U = uh.reshape(2, n, n)
+    ref = np.stack([U[:, i, j] for i, j in nodes])
+    np.testing.assert_allclose(got, ref, atol=1e-9 * np.abs(uh).max())
+    elems = np.array([[0, 0], [5, 9], [14, 14]])
+    h = 1.0 / (n - 1)
+    st = u.strain(pr.grid, elems)
+    for e, (i, j) in enumerate(elems):
+        ux = 0.5 * ((U[0, i + 1, j] - U[0, i, j]) + (U[0, i + 1, j + 1] - U[0, i, j + 1])) / h
+        vy = 0.5 * ((U[1, i, j + 1] - U[1, i, j]) + (U[1, i + 1, j + 1] - U[1, i + 1, j])) / h
+        assert st[e, 0] == pytest.approx(ux, abs=1e-8 * np.abs(uh).max() / h)
+        assert st[e, 1] == pytest.approx(vy, abs=1e-8 * np.abs(uh).max() / h)
