@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the QTT linear-elasticity solve (AMEn sweep) on one or more GPUs.
+
+One step = one complete solve A u = f of the 2D plane-strain steel plate on 2^10 x 2^10 nodes
+(2,097,152 unknowns; E = 210 GPa, nu = 0.3, clamped left edge, gravity rho = 7850 plus a
+downward traction of 1 MN/m^2 on the right edge; QTT with 10 levels, rank cap 64), from a
+seeded rank-2 start, to relative energy-norm error 1e-6 by the mixed-precision path (binary32
+sweeps inside binary64 iterative refinement).  The operator and load are built once on the
+device before timing; the e2e leg rebuilds them from the host parameters every step.
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (one solve stream per
+GPU, no collective on the data path): ``value`` is the total solves per second of all ranks.
+
+``--impl reference`` times the CPU FP64 oracle (plain numpy TT toolkit + AMEn) on the host on a
+bounded sample of the same workload and prints the same JSON line with ``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "TT-solve time to rel. energy err 1e-6 (mixed vs FP64); solves/s, p50/p99 latency"
+UNIT = "solves/s"
+
+# Peaks used for the roofline fractions.  HBM / bf16 come from the measured peaks file when it is
+# present; the CUDA-core peaks are derived from the SM count, lanes per SM and the maximum clock.
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 binary64 (CUDA cores and tensor cores alike)
+
+
+def fp32_simt_peak_gflops(mhz: float = SM_MAX_MHZ) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2.0 * mhz * 1e-3
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def workload(levels: int, rank_cap: int, precision: str):
+    from paper_2501_12151_gb300 import workloads as W
+    pr = W.steel_plate_2d(levels=levels, rank_cap=rank_cap, tol=1e-9, precision=precision)
+    pr.opts.refine_tol = 1e-6
+    return pr
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                                 parts[5], parts[6], parts[7], parts[8]))
+                except ValueError:
+                    continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------------------------
+
+def dist_init(gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(levels: int, rank_cap: int, sweeps: int):
+    """Time the FP64 oracle AMEn on the same problem for a bounded number of sweeps.
+
+    The sample is the oracle's own construction of the operator and load plus ``sweeps`` AMEn
+    sweeps; the solve time is extrapolated linearly to the number of sweeps the oracle needs for
+    a full solve of this problem (measured once as ``full_sweeps`` when it is affordable, else
+    the sample's last-sweep cost times the sweeps the GPU solve used)."""
+    import numpy as np
+    from oracle import amen, fem, mpo
+    from paper_2501_12151_gb300 import workloads as W
+    pr = workload(levels, rank_cap, "fp64")
+    threads = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    Ao, _ = mpo.stiffness_mpo(pr.grid, pr.material)
+    _, M = fem.assemble(pr.grid, pr.material)
+    fv = fem.load_vector(pr.grid, pr.material, pr.loads, M) * np.tile(~fem.constrained_nodes(pr.grid), pr.grid.dim)
+    fo = mpo.load_tt_dense(fv, pr.grid)
+    t_build = time.perf_counter() - t0
+    x0 = W.random_tt(1, W.qtt_modes(pr.grid.dim, levels), [1] + [2] * levels + [1])
+    t0 = time.perf_counter()
+    _, info = amen.amen_solve(Ao, fo, x0, tol=pr.opts.tol, rmax=rank_cap, nswp=sweeps)
+    t_sweeps = time.perf_counter() - t0
+    return {"t_build": t_build, "t_sweeps": t_sweeps, "sweeps": info.sweeps, "threads": threads}
+
+
+# ---------------------------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the tnfem library has no CPU path)")
+    torch.cuda.set_device(local)
+    from paper_2501_12151_gb300 import tnfem
+    stream = torch.cuda.current_stream()
+    ctx = tnfem.Context(local, stream=stream.cuda_stream, torch_alloc=True)
+
+    pr = workload(args.levels, args.rank_cap, args.precision)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def step():
+        u, info = ctx.solve(A, f, pr.opts)
+        return u, info
+
+    for _ in range(args.warmup):
+        u, info = step()
+    torch.cuda.synchronize()
+
+    lat = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ctx.launches
+    ctx.profile_start(args.prof_every)
+    infos = []
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            u, info = step()
+            ev[i][1].record(stream)
+            infos.append(info)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = ctx.launches - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    prof = {c: ctx.profile_read(c) for c in tnfem.PROF_CLASSES}
+    ctx.profile_start(0)
+    total_ms_max = max_over_ranks(total_ms, world)
+
+    # end to end through the public API: host parameters -> build -> solve -> cores to host
+    e2e = None
+    if not args.no_e2e:
+        h2d = 0
+        hs, _ = tnfem.host_stiffness(pr.grid, pr.material)
+        hl = tnfem.host_load(pr.grid, pr.material, pr.loads)
+        h2d = sum(c.nbytes for c in hs) + sum(c.nbytes for c in hl)
+        e2e_steps = max(1, min(args.steps, 3))
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(e2e_steps):
+            A2 = ctx.stiffness(pr.grid, pr.material)
+            f2 = ctx.load(pr.grid, pr.material, pr.loads)
+            u2, _ = ctx.solve(A2, f2, pr.opts)
+            cores = u2.cores()
+            d2h = sum(c.nbytes for c in cores)
+            del A2, f2, u2
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    # FP64 path for the "mixed vs FP64" comparison (one solve, same problem)
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision == "mixed":
+        o64 = workload(args.levels, args.rank_cap, "fp64").opts
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            u64, i64 = ctx.solve(A, f, o64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        err_mixed_vs_fp64 = A.energy_norm(u, u64) / A.energy_norm(u64)
+        fp64 = {"ms_per_solve": ms64, "sweeps": i64["sweeps"], "converged": bool(i64["converged"]),
+                "mixed_speedup": ms64 / (total_ms / args.steps), "rel_energy_diff_mixed_vs_fp64": err_mixed_vs_fp64}
+
+    if rank != 0:
+        return None
+
+    # roofline of the dominant contraction kernel class
+    pk = measured_peaks()
+    cls = "contract32" if args.precision == "mixed" else "contract64"
+    p = prof[cls]
+    achieved = (p["flops"] / (p["ms"] * 1e-3) * 1e-12) if p["ms"] > 0 else 0.0
+    if cls == "contract32":
+        peak = fp32_simt_peak_gflops() * 1e-3
+        peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (CUDA-core binary32 GEMM)"
+    else:
+        peak = FP64_NOMINAL_GFLOPS * 1e-3
+        peak_note = "nominal GB300 binary64 rate (1.25 TFLOP/s)"
+    share = {c: (prof[c]["ms"] * (prof[c]["launches"] / max(1, prof[c]["sampled"]))) for c in prof}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "gemm_kernel<float>" if cls == "contract32" else "gemm_kernel<double>",
+                "peak_source": peak_note,
+                "launches": p["launches"], "sampled_launches": p["sampled"],
+                "avg_launch_us": (p["ms"] * 1e3 / p["sampled"]) if p["sampled"] else None,
+                "flops_per_launch": (p["flops"] / p["sampled"]) if p["sampled"] else None,
+                "est_device_ms_by_class": share}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+        s = oracle_sample(args.levels, args.rank_cap, args.cpu_sweeps)
+        # scale the sampled sweeps to a full solve by the sweep count of the GPU binary64 solve
+        full_sweeps = fp64["sweeps"] if fp64 else max(1, infos[-1]["sweeps"])
+        per_sweep = s["t_sweeps"] / max(1, s["sweeps"])
+        t_solve = s["t_build"] + per_sweep * full_sweeps
+        cpu = {"value": 1.0 / t_solve, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+               "sample": (f"oracle operator/load build ({s['t_build']:.1f} s) + first {s['sweeps']} FP64 AMEn "
+                          f"sweeps ({s['t_sweeps']:.1f} s) of the same problem, extrapolated at the mean "
+                          f"sweep cost to {full_sweeps} sweeps (the GPU binary64 solve's count)")}
+
+    ms_per_step = total_ms_max / args.steps
+    last = infos[-1]
+    out = {
+        "metric": METRIC,
+        "value": world * args.steps / (total_ms_max * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"2D plane-strain steel plate, 2^{args.levels}x2^{args.levels} nodes "
+                               f"({2 * 4 ** args.levels} DOF), QTT {args.levels} levels, rank cap {args.rank_cap}, "
+                               f"{args.precision}, rel. energy err target 1e-6",
+                   "levels": args.levels, "rank_cap": args.rank_cap, "precision": args.precision,
+                   "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)"},
+        "accuracy": {"energy_err_est": last["energy_err_est"], "refines": last["refines"], "sweeps": last["sweeps"],
+                     "max_rank": last["max_rank"], "local_iters": last["local_iters"],
+                     "converged": bool(last["converged"])},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "e2e": e2e,
+        "fp64": fp64,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    times = []
+    s = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = oracle_sample(args.levels, args.rank_cap, args.cpu_sweeps)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    full_sweeps = args.ref_full_sweeps
+    per_solve = [s["t_build"] + (s["t_sweeps"] / max(1, s["sweeps"])) * full_sweeps for _ in times]
+    value = 1.0 / statistics.mean(per_solve)
+    sample = (f"oracle operator/load build + first {s['sweeps']} FP64 AMEn sweeps per step, extrapolated at "
+              f"the mean sweep cost to {full_sweeps} sweeps per solve")
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 / value,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"2D plane-strain steel plate, 2^{args.levels}x2^{args.levels} nodes "
+                               f"({2 * 4 ** args.levels} DOF), QTT {args.levels} levels, rank cap {args.rank_cap}, "
+                               f"{args.precision}, rel. energy err target 1e-6",
+                   "levels": args.levels, "rank_cap": args.rank_cap, "precision": args.precision,
+                   "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": s["threads"], "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--levels", type=int, default=10)
+    ap.add_argument("--rank-cap", type=int, default=64)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--prof-every", type=int, default=8, help="time every n-th launch of each kernel class")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--ref-full-sweeps", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

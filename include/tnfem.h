@@ -95,6 +95,7 @@ typedef struct {
   int max_refine;      /* MIXED: maximum outer refinement steps */
   uint64_t seed;       /* seed of the counter-based generator for the start guess / enrichment */
   int local_maxit;     /* cap on conjugate-gradient iterations per local solve */
+  int no_precond;      /* 0: block-Jacobi preconditioned local solves (default); 1: plain CG */
 } tnfem_solve_opts;
 
 typedef struct {
@@ -126,6 +127,25 @@ const char* tnfem_last_error(const tnfem_ctx* ctx);
 tnfem_status tnfem_set_stream(tnfem_ctx* ctx, void* stream);
 /* Number of kernels this context has launched since creation (for accounting). */
 long long tnfem_kernel_launches(const tnfem_ctx* ctx);
+
+/* ---- sampled kernel timing (tracing; not part of the method) ------------------------------ *
+ * Kernel classes: the sweep's dense contractions (local matvec, environments, projections) in
+ * binary32 and in binary64, the Krylov vector kernels, Householder QR, Jacobi SVD, the rest.  */
+#define TNFEM_PROF_CONTRACT32 0
+#define TNFEM_PROF_CONTRACT64 1
+#define TNFEM_PROF_KRYLOV 2
+#define TNFEM_PROF_QR 3
+#define TNFEM_PROF_SVD 4
+#define TNFEM_PROF_OTHER 5
+#define TNFEM_PROF_CLASSES 6
+/* Start (or restart) sampling: from now on every `every`-th launch of each class is bracketed by
+ * two CUDA events on the context's stream; every <= 0 stops sampling.  Counters are reset. */
+tnfem_status tnfem_profile_start(tnfem_ctx* ctx, int every);
+/* Synchronise the stream and report class `cls` since tnfem_profile_start: launches seen,
+ * launches sampled, summed device milliseconds of the sampled launches and their summed
+ * algorithmic flops and bytes (any output pointer may be NULL). */
+tnfem_status tnfem_profile_read(tnfem_ctx* ctx, int cls, long long* launches, long long* sampled,
+                                double* ms, double* flops, double* bytes);
 
 /* ---- assembly (Algorithm 1, Section 5.2 / 5.3) ------------------------------------------- */
 

@@ -24,6 +24,7 @@
 
 #include "amen.h"
 #include "internal.h"
+#include "precond.h"
 
 namespace tnfem {
 
@@ -80,28 +81,31 @@ __global__ void __launch_bounds__(RT) cg_dot_kernel(const T* __restrict__ x, con
   block_partial_out(s, sh, part);
 }
 
-// alpha = rr / pAp; x += alpha p; r -= alpha Ap; partial sums of the new r.r
+// Stop test on r.r (partials part_rr), then alpha = r.z / pAp; x += alpha p; r -= alpha Ap;
+// partial sums of the new r.r.  Without a preconditioner z = r and part_rz aliases part_rr.
 // ctl[0]: 0 running, 1 converged, 2 breakdown; ctl[1]: iterations done
 template <typename T>
 __global__ void __launch_bounds__(RT) cg_update1_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                         const T* __restrict__ Ap, size_t N,
                                                         const double* __restrict__ part_rr,
+                                                        const double* __restrict__ part_rz,
                                                         const double* __restrict__ part_pAp,
                                                         double* __restrict__ part_rr_new, int* __restrict__ ctl,
                                                         double stop2) {
   if (ctl[0]) return;
   __shared__ double sh[32];
   const double rr = block_reduce_partials(part_rr, sh);
+  const double rz = block_reduce_partials(part_rz, sh);
   const double pAp = block_reduce_partials(part_pAp, sh);
   if (rr <= stop2) {
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[0] = 1;
     return;
   }
-  if (!(pAp > 0.0) || !isfinite(pAp)) {
+  if (!(pAp > 0.0) || !isfinite(pAp) || !(rz > 0.0)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[0] = 2;
     return;
   }
-  const T alpha = (T)(rr / pAp);
+  const T alpha = (T)(rz / pAp);
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
@@ -113,17 +117,18 @@ __global__ void __launch_bounds__(RT) cg_update1_kernel(T* __restrict__ x, T* __
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl[1] += 1;
 }
 
+// p = z + beta p with beta = (r.z)_new / (r.z)_old
 template <typename T>
-__global__ void __launch_bounds__(RT) cg_update2_kernel(T* __restrict__ p, const T* __restrict__ r, size_t N,
-                                                        const double* __restrict__ part_rr_new,
-                                                        const double* __restrict__ part_rr, const int* __restrict__ ctl) {
+__global__ void __launch_bounds__(RT) cg_update2_kernel(T* __restrict__ p, const T* __restrict__ z, size_t N,
+                                                        const double* __restrict__ part_rz_new,
+                                                        const double* __restrict__ part_rz, const int* __restrict__ ctl) {
   if (ctl[0]) return;
   __shared__ double sh[32];
-  const double rn = block_reduce_partials(part_rr_new, sh);
-  const double ro = block_reduce_partials(part_rr, sh);
+  const double rn = block_reduce_partials(part_rz_new, sh);
+  const double ro = block_reduce_partials(part_rz, sh);
   const T beta = (T)(rn / ro);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = r[i] + beta * p[i];
+    p[i] = z[i] + beta * p[i];
 }
 
 // d = a - b (precision T), partial sums of d.d
@@ -210,7 +215,7 @@ class Amen {
   const double* A64cur(int k) const { return A_->p64[o_][k]; }
   // environments: fam -> side (0: left of original bond, 1: right) -> original bond
   T*& envT(int fam, int side, int bond) { return envT_[fam][side][bond]; }
-  double*& envS(int fam, int side, int bond) { return envS_[fam][side][bond]; }
+  double*& envS(int fam, int side, int bond) { return envS_[side][fam][bond]; }
   // current-orientation left / right environment of current core k
   int side_left() const { return o_ == 0 ? 0 : 1; }
   int side_right() const { return o_ == 0 ? 1 : 0; }
@@ -262,6 +267,9 @@ class Amen {
   DArr<T> wsT_, y_, g_, Bx_, r_, p_, Ap_, tmpA_, tmpB_, U_, S_, Vt_, Ue_, Q_, R_, Vn_, svdw_, qrw_, crz_, crs_, nxt_;
   DArr<double> ws64_, g64_, c64_, part_;
   DArr<int> ctl_;
+  DArr<T> z_, bjw_;     // preconditioned residual, block-Jacobi set-up workspace
+  DArr<float> bjP_;     // block-Jacobi inverses
+  long long precond_solves_ = 0;
   double* host_ = nullptr;
   double flops_ = 0.0;
   long long iters_ = 0;
@@ -385,7 +393,8 @@ void Amen<T>::setup(const tnfem_tt* x0) {
   crz_ = DArr<T>(ctx_, maxmn);
   crs_ = DArr<T>(ctx_, maxmn);
   nxt_ = DArr<T>(ctx_, maxmn + (size_t)maxr * maxr * 64);
-  part_ = DArr<double>(ctx_, 4 * kReduceBlocks + 8);
+  part_ = DArr<double>(ctx_, 6 * kReduceBlocks + 8);
+  z_ = DArr<T>(ctx_, maxloc);
   ctl_ = DArr<int>(ctx_, 4);
   host_ = ctx_->host_pinned;
 
@@ -539,15 +548,26 @@ int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
   const T* PL = EL(0, k);
   const T* PR = ER(0, k);
   const T* Ak = Acur(k);
-  double* prr0 = part_.p;
-  double* prr1 = part_.p + kReduceBlocks;
-  double* ppap = part_.p + 2 * kReduceBlocks;
+  double* prr[2] = {part_.p, part_.p + kReduceBlocks};
+  double* prz_b[2] = {part_.p + 2 * kReduceBlocks, part_.p + 3 * kReduceBlocks};
+  double* ppap = part_.p + 4 * kReduceBlocks;
   int* ctl = ctl_.p;
+  // block-Jacobi preconditioner of this local system (falls back to plain CG when unusable)
+  bool pre = false;
+  if (prm_.precond && bj_fits(r0, n, r1)) {
+    const size_t need = bj_work_elems(r0, n, r1, a0, a1);
+    bjw_.ensure(ctx_, need);
+    bjP_.ensure(ctx_, (size_t)r1 * r0 * n * r0 * n);
+    pre = bj_setup<T>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, bjP_.p, bjw_.p, bjw_.n, ctl_.p + 2);
+  }
+  T* z = pre ? z_.p : r_.p;
+  double** prz = pre ? prz_b : prr;
   TN_CHECK_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), ctx_->stream));
   local_matvec<T>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, Bx_.p, wsT_.p, wsT_.n);
   count_apply(r0, r1, r0, r1, n, a0, a1);
-  cg_init_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(g, Bx_.p, r_.p, p_.p, N, prr0);
+  cg_init_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(g, Bx_.p, r_.p, p_.p, N, prr[0]);
   count_launch(ctx_);
+  if (pre) bj_apply<T>(ctx_, r0, n, r1, bjP_.p, r_.p, z_.p, p_.p, prz[0], nullptr);
   const double stop2 = rtol * rtol * gnorm * gnorm;
   int done_it = 0;
   int cur = 0;
@@ -556,14 +576,24 @@ int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
   while (it < maxit) {
     int chunk = std::min(8, maxit - it);
     for (int c = 0; c < chunk; ++c) {
-      double* prr = cur ? prr1 : prr0;
-      double* prn = cur ? prr0 : prr1;
+      const int nx = cur ^ 1;
       local_matvec<T>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, p_.p, Ap_.p, wsT_.p, wsT_.n, ctl);
-      cg_dot_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(p_.p, Ap_.p, N, ppap, ctl);
-      cg_update1_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(y, r_.p, p_.p, Ap_.p, N, prr, ppap, prn, ctl, stop2);
-      cg_update2_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(p_.p, r_.p, N, prn, prr, ctl);
+      {
+        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 2.0 * N * sizeof(T));
+        cg_dot_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(p_.p, Ap_.p, N, ppap, ctl);
+      }
+      {
+        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 6.0 * N, 6.0 * N * sizeof(T));
+        cg_update1_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(y, r_.p, p_.p, Ap_.p, N, prr[cur], prz[cur], ppap,
+                                                                     prr[nx], ctl, stop2);
+      }
+      if (pre) bj_apply<T>(ctx_, r0, n, r1, bjP_.p, r_.p, z_.p, nullptr, prz[nx], ctl);
+      {
+        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 3.0 * N * sizeof(T));
+        cg_update2_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(p_.p, z, N, prz[nx], prz[cur], ctl);
+      }
       count_launch(ctx_, 3);
-      cur ^= 1;
+      cur = nx;
     }
     it += chunk;
     check_launch(ctx_, "cg");
@@ -575,6 +605,7 @@ int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
     if (h[0]) break;
   }
   for (int i = 0; i < done_it; ++i) count_apply(r0, r1, r0, r1, n, a0, a1);
+  if (pre) ++precond_solves_;
   return done_it;
 }
 

@@ -22,6 +22,7 @@ struct AmenParams {
   int max_sweeps = 40;
   int local_maxit = 500;    // conjugate-gradient iterations per local solve
   double resid_damp = 2.0;  // local solves stop at tol / resid_damp
+  bool precond = true;      // block-Jacobi preconditioned conjugate gradients for the local solves
   uint64_t seed = 0;
   bool verbose = false;
 };

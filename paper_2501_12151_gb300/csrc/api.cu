@@ -162,6 +162,8 @@ tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, con
   ip.max_sweeps = std::max(2, std::min(o->max_sweeps, 12));
   ip.local_maxit = o->local_maxit > 0 ? o->local_maxit : 500;
   ip.seed = o->seed;
+  ip.precond = o->no_precond == 0;
+  ip.verbose = getenv("TNFEM_VERBOSE") != nullptr;
   tnfem_tt* u = x0 ? tt_clone(x0) : nullptr;
   const double fnorm = energy_norm(ctx, A, f, nullptr);  // scale reference (any norm works)
   (void)fnorm;
@@ -245,6 +247,7 @@ tnfem_status tnfem_create(int device, void* stream, tnfem_alloc_fn alloc_fn, tnf
 
 void tnfem_destroy(tnfem_ctx* ctx) {
   if (!ctx) return;
+  prof_release(ctx);
   if (ctx->scratch) dfree(ctx, ctx->scratch);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   delete ctx;
@@ -351,6 +354,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
       p.max_sweeps = opts->max_sweeps;
       p.local_maxit = opts->local_maxit > 0 ? opts->local_maxit : 500;
       p.seed = opts->seed;
+      p.precond = opts->no_precond == 0;
       p.verbose = getenv("TNFEM_VERBOSE") != nullptr;
       AmenStats s;
       res = amen_solve(ctx, A, {AmenSource{f, false, 1.0}}, p, x0, false, s);

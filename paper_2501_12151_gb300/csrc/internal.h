@@ -49,6 +49,21 @@ struct tnfem_ctx {
   double* scratch = nullptr;  // kScratchDoubles doubles
   // pinned host staging for small device->host reads
   double* host_pinned = nullptr;
+  // sampled launch timing (see tnfem_profile_start): events around every `prof_every`-th launch
+  // of each kernel class, resolved on tnfem_profile_read
+  struct ProfEv {
+    cudaEvent_t a, b;
+    int cls;
+    double flops, bytes;
+  };
+  int prof_every = 0;
+  long long prof_seen[TNFEM_PROF_CLASSES] = {};
+  long long prof_sampled[TNFEM_PROF_CLASSES] = {};
+  double prof_ms[TNFEM_PROF_CLASSES] = {};
+  double prof_flops[TNFEM_PROF_CLASSES] = {};
+  double prof_bytes[TNFEM_PROF_CLASSES] = {};
+  std::vector<ProfEv> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
 };
 
 namespace tnfem {
@@ -60,6 +75,17 @@ void* dalloc(tnfem_ctx* ctx, size_t bytes);
 void dfree(tnfem_ctx* ctx, void* p);
 void sync(tnfem_ctx* ctx);
 inline void count_launch(tnfem_ctx* ctx, int n = 1) { ctx->launches += n; }
+
+// Brackets one kernel launch of class `cls` with a pair of events on the context's stream when
+// profiling samples it; `flops` / `bytes` are the launch's algorithmic work and traffic.
+struct ProfScope {
+  tnfem_ctx* ctx;
+  int idx = -1;
+  ProfScope(tnfem_ctx* c, int cls, double flops, double bytes);
+  ~ProfScope();
+};
+void prof_resolve(tnfem_ctx* ctx);
+void prof_release(tnfem_ctx* ctx);
 void check_launch(tnfem_ctx* ctx, const char* what);
 
 // RAII device array

@@ -289,10 +289,17 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
   splits = (g.K + kchunk - 1) / kchunk;
   dim3 grid(tiles_n, tiles_m, g.batch * splits);
   TN_REQUIRE(g.batch * (long long)splits < 65536, "gemm: batch too large");
-  gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, skip);
+  {
+    const double mnk = (double)g.M * g.N * g.K * g.batch;
+    const double words = ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N) * g.batch;
+    ProfScope ps(ctx, sizeof(T) == 8 ? TNFEM_PROF_CONTRACT64 : TNFEM_PROF_CONTRACT32, 2.0 * mnk,
+                 words * sizeof(T));
+    gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, skip);
+  }
   count_launch(ctx);
   if (splits > 1) {
     long long total = (long long)g.batch * g.M * g.N;
+    ProfScope ps(ctx, TNFEM_PROF_OTHER, (double)total * splits, (double)total * (splits + 1) * sizeof(T));
     splitk_reduce_kernel<T><<<grid_for(total), 256, 0, ctx->stream>>>(g, alpha, beta, C, work, splits, skip);
     count_launch(ctx);
   }

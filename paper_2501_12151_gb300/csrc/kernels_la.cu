@@ -3,6 +3,7 @@
 // SVD used for TT truncation.  One CTA of 1024 threads works on a matrix held in global
 // memory (L2/L1-resident at these sizes); all loops have fixed trip counts, nothing waits on
 // another block.
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.h"
@@ -233,6 +234,8 @@ size_t svd_work_elems(int m, int n) { return (size_t)m * n + (size_t)n * n + (si
 template <typename T>
 void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
   if (m <= 0 || n <= 0) return;
+  const int k = std::min(m, n);
+  ProfScope ps(ctx, TNFEM_PROF_QR, 4.0 * m * n * (double)k, (double)(2 * m * n + m * k + k * n) * sizeof(T));
   qr_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, Q, R, work);
   count_launch(ctx);
   check_launch(ctx, "qr");
@@ -245,6 +248,7 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   T* G = work;
   T* V = G + (size_t)m * n;
   T* sig = V + (size_t)n * n;
+  ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
   svd_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, U, S, Vt, G, V, sig, sizeof(T) == 8 ? 60 : 40);
   count_launch(ctx);
   check_launch(ctx, "svd");

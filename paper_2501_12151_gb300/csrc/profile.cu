@@ -1,0 +1,114 @@
+// Sampled launch timing.  When enabled, every `prof_every`-th launch of a kernel class is
+// bracketed by two CUDA events recorded on the context's stream, together with that launch's
+// algorithmic flops and bytes; tnfem_profile_read synchronises, resolves the pending event pairs
+// into per-class sums and returns the events to a pool.  Sampling keeps the event overhead small
+// on the launch-dense Krylov loop while still timing every kind of launch the sweep makes.
+#include "internal.h"
+
+namespace tnfem {
+
+namespace {
+
+cudaEvent_t take_event(tnfem_ctx* ctx) {
+  if (!ctx->prof_pool.empty()) {
+    cudaEvent_t e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  TN_CHECK_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+}  // namespace
+
+ProfScope::ProfScope(tnfem_ctx* c, int cls, double flops, double bytes) : ctx(c) {
+  if (ctx->prof_every <= 0 || cls < 0 || cls >= TNFEM_PROF_CLASSES) return;
+  long long seen = ctx->prof_seen[cls]++;
+  if (seen % ctx->prof_every != 0) return;
+  tnfem_ctx::ProfEv ev{take_event(ctx), take_event(ctx), cls, flops, bytes};
+  TN_CHECK_CUDA(cudaEventRecord(ev.a, ctx->stream));
+  ctx->prof_pending.push_back(ev);
+  idx = (int)ctx->prof_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx < 0) return;
+  // a failed record only loses this sample; destructors must not throw
+  if (cudaEventRecord(ctx->prof_pending[idx].b, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->prof_pending[idx].cls = -1;
+  }
+}
+
+void prof_resolve(tnfem_ctx* ctx) {
+  if (ctx->prof_pending.empty()) return;
+  TN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& ev : ctx->prof_pending) {
+    if (ev.cls >= 0) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) {
+        ctx->prof_sampled[ev.cls] += 1;
+        ctx->prof_ms[ev.cls] += ms;
+        ctx->prof_flops[ev.cls] += ev.flops;
+        ctx->prof_bytes[ev.cls] += ev.bytes;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    ctx->prof_pool.push_back(ev.a);
+    ctx->prof_pool.push_back(ev.b);
+  }
+  ctx->prof_pending.clear();
+}
+
+void prof_release(tnfem_ctx* ctx) {
+  for (auto& ev : ctx->prof_pending) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  ctx->prof_pending.clear();
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+  ctx->prof_pool.clear();
+}
+
+}  // namespace tnfem
+
+using namespace tnfem;
+
+extern "C" {
+
+tnfem_status tnfem_profile_start(tnfem_ctx* ctx, int every) {
+  if (!ctx) return TNFEM_E_INVALID;
+  try {
+    prof_resolve(ctx);
+  } catch (const Error& e) {
+    ctx->err = e.what();
+    return e.status;
+  }
+  ctx->prof_every = every > 0 ? every : 0;
+  for (int c = 0; c < TNFEM_PROF_CLASSES; ++c) {
+    ctx->prof_seen[c] = ctx->prof_sampled[c] = 0;
+    ctx->prof_ms[c] = ctx->prof_flops[c] = ctx->prof_bytes[c] = 0.0;
+  }
+  return TNFEM_OK;
+}
+
+tnfem_status tnfem_profile_read(tnfem_ctx* ctx, int cls, long long* launches, long long* sampled, double* ms,
+                                double* flops, double* bytes) {
+  if (!ctx || cls < 0 || cls >= TNFEM_PROF_CLASSES) return TNFEM_E_INVALID;
+  try {
+    prof_resolve(ctx);
+  } catch (const Error& e) {
+    ctx->err = e.what();
+    return e.status;
+  }
+  if (launches) *launches = ctx->prof_seen[cls];
+  if (sampled) *sampled = ctx->prof_sampled[cls];
+  if (ms) *ms = ctx->prof_ms[cls];
+  if (flops) *flops = ctx->prof_flops[cls];
+  if (bytes) *bytes = ctx->prof_bytes[cls];
+  return TNFEM_OK;
+}
+
+}  // extern "C"

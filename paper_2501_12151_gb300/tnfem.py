@@ -48,7 +48,7 @@ class CLoad(C.Structure):
 class COpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("rank_cap", C.c_int), ("kickrank", C.c_int), ("max_sweeps", C.c_int),
                 ("precision", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int),
-                ("seed", C.c_uint64), ("local_maxit", C.c_int)]
+                ("seed", C.c_uint64), ("local_maxit", C.c_int), ("no_precond", C.c_int)]
 
 
 class CInfo(C.Structure):
@@ -109,6 +109,10 @@ _sig("tnfem_op_local_matvec", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, 
 _sig("tnfem_op_env_left", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_qr", _i, [_vp, _i, _i, _vp, _vp, _vp])
 _sig("tnfem_op_svd", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp])
+_sig("tnfem_profile_start", _i, [_vp, _i])
+_sig("tnfem_profile_read", _i, [_vp, _i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pd, _pd, _pd])
+
+PROF_CLASSES = {"contract32": 0, "contract64": 1, "krylov": 2, "qr": 3, "svd": 4, "other": 5}
 
 
 # ---------------------------------------------------------------------------------------
@@ -174,6 +178,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.max_refine = int(o.max_refine)
     co.seed = int(o.seed)
     co.local_maxit = int(local_maxit)
+    co.no_precond = 0 if getattr(o, "precond", True) else 1
     return co
 
 
@@ -277,6 +282,18 @@ class Context:
 
     def set_stream(self, stream: int):
         self.check(lib.tnfem_set_stream(self.h, C.c_void_p(stream)))
+
+    def profile_start(self, every: int = 1):
+        """Time every ``every``-th launch of each kernel class with CUDA events (0 stops)."""
+        self.check(lib.tnfem_profile_start(self.h, int(every)))
+
+    def profile_read(self, cls: str) -> dict:
+        """Launches seen / sampled, device ms, algorithmic flops and bytes of the sampled launches."""
+        n, s = C.c_longlong(), C.c_longlong()
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        self.check(lib.tnfem_profile_read(self.h, PROF_CLASSES[cls], C.byref(n), C.byref(s), C.byref(ms),
+                                          C.byref(fl), C.byref(by)))
+        return {"launches": n.value, "sampled": s.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
     # builders
     def stiffness(self, grid: Grid, mat: Material) -> "Mpo":

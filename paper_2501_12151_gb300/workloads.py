@@ -87,6 +87,7 @@ class SolveOpts:
     refine_tol: float = 1e-6
     max_refine: int = 20
     seed: int = 0
+    precond: bool = True      # block-Jacobi preconditioned local solves
 
 
 @dataclass

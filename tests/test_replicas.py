@@ -1,0 +1,56 @@
+"""Host-side logic of the multi-GPU bench: independent replicas, one solve stream per rank, no
+collective on the data path; only a barrier and a max-reduction of the timer cross ranks.  Runs
+as two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        bench.barrier(world)
+        # each replica reports its own elapsed time; the job time is the slowest rank's
+        t = bench.max_over_ranks(1.0 + rank, world)
+        out[rank] = t
+        bench.barrier(world)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_rank():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert dict(out) == {0: 2.0, 1: 2.0}
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    ns = type("A", (), {"levels": 3, "rank_cap": 8, "steps": 1, "warmup": 0, "cpu_sweeps": 1,
+                        "ref_full_sweeps": 2, "precision": "fp64"})()
+    assert bench.run_reference(ns) is None
