@@ -241,7 +241,7 @@ def run_ours(args):
         hs, _ = tnfem.host_stiffness(pr.grid, pr.material)
         hl = tnfem.host_load(pr.grid, pr.material, pr.loads)
         h2d = sum(c.nbytes for c in hs) + sum(c.nbytes for c in hl)
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, args.e2e_steps)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -260,7 +260,7 @@ def run_ours(args):
 
     # FP64 path for the "mixed vs FP64" comparison (one solve, same problem)
     fp64 = None
-    if args.fp64_steps > 0 and args.precision == "mixed":
+    if args.fp64_steps > 0 and args.precision != "fp64":
         o64 = workload(args.levels, args.rank_cap, "fp64").opts
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -280,7 +280,7 @@ def run_ours(args):
 
     # roofline of the dominant contraction kernel class
     pk = measured_peaks()
-    cls = "contract32" if args.precision == "mixed" else "contract64"
+    cls = "contract32" if args.precision != "fp64" else "contract64"
     p = prof[cls]
     achieved = (p["flops"] / (p["ms"] * 1e-3) * 1e-12) if p["ms"] > 0 else 0.0
     if cls == "contract32":
@@ -325,7 +325,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "dtype": "f32+f64" if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": {"workload": f"2D plane-strain steel plate, 2^{args.levels}x2^{args.levels} nodes "
                                f"({2 * 4 ** args.levels} DOF), QTT {args.levels} levels, rank cap {args.rank_cap}, "
@@ -398,13 +398,14 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=10)
     ap.add_argument("--rank-cap", type=int, default=64)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "mixed-local", "fp64"], default="mixed")
     ap.add_argument("--prof-every", type=int, default=8, help="time every n-th launch of each kernel class")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-sweeps", type=int, default=3)
     ap.add_argument("--ref-full-sweeps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
     args = ap.parse_args(argv)
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

@@ -82,7 +82,13 @@ typedef struct {
   double scale;         /* FOURIER */
 } tnfem_load;
 
-typedef enum { TNFEM_FP64 = 0, TNFEM_MIXED = 1 } tnfem_precision;
+/* FP64: every step in binary64.
+ * MIXED: binary32 AMEn solves of the correction equation A e = f - A u inside an outer iterative
+ *   refinement whose residual projections and u + e rounding are binary64.
+ * MIXED_LOCAL: binary64 sweep (environments, projections, QR, SVD) whose local systems are solved
+ *   by binary32 preconditioned CG, refined against the binary64 local residual until it meets the
+ *   same tolerance as FP64. */
+typedef enum { TNFEM_FP64 = 0, TNFEM_MIXED = 1, TNFEM_MIXED_LOCAL = 2 } tnfem_precision;
 
 typedef struct {
   double tol;          /* sweep stop: largest local residual or local update <= tol; truncation

@@ -170,6 +170,18 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, double* __r
   if (threadIdx.x == 0) *out = s;
 }
 
+// dst = (float)(src * s)
+__global__ void scale_to_float_kernel(float* __restrict__ dst, const double* __restrict__ src, double s, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)(src[i] * s);
+}
+
+// y += s * (double)d
+__global__ void add_scaled_float_kernel(double* __restrict__ y, const float* __restrict__ d, double s, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += s * (double)d[i];
+}
+
 inline int nblk(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + RT - 1) / RT, kReduceBlocks)); }
 
 template <typename T> struct Prec;
@@ -235,6 +247,19 @@ class Amen {
   void envs_at(int k, bool with_z);  // compute left envs of bond k+1 from core k
   void core_step(int k, AmenStats& st);
   int cg(int k, T* y, const T* g, double gnorm, double rtol);
+  // buffers of one preconditioned conjugate-gradient run in precision U
+  template <typename U>
+  struct CgBufs {
+    U *Bx, *r, *p, *Ap, *z, *ws;
+    size_t wsn;
+    bool pre;
+  };
+  template <typename U>
+  bool setup_pre(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, DArr<U>& work);
+  template <typename U>
+  int pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, U* y, const U* g,
+              double gnorm, double rtol, const CgBufs<U>& b);
+  int cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol);
   void source_proj(int k, bool bra_z_left, bool bra_z_right, double* out, int ry0, int ry1);
   double* bra64(bool z, int k, int r0, int r1);
   void count_apply(int ry0, int ry1, int rx0, int rx1, int n, int a0, int a1) {
@@ -270,6 +295,11 @@ class Amen {
   DArr<T> z_, bjw_;     // preconditioned residual, block-Jacobi set-up workspace
   DArr<float> bjP_;     // block-Jacobi inverses
   long long precond_solves_ = 0;
+  // binary32 shadow of the local solve (binary64 sweep with binary32 local solves)
+  DArr<float> PL32_, PR32_, g32_, y32_, Bx32_, r32_, p32_, Ap32_, z32_, ws32_, bjw32_;
+  DArr<double> d64_;
+  long long local_refines_ = 0;
+  long long breakdowns_ = 0;
   double* host_ = nullptr;
   double flops_ = 0.0;
   long long iters_ = 0;
@@ -395,6 +425,19 @@ void Amen<T>::setup(const tnfem_tt* x0) {
   nxt_ = DArr<T>(ctx_, maxmn + (size_t)maxr * maxr * 64);
   part_ = DArr<double>(ctx_, 6 * kReduceBlocks + 8);
   z_ = DArr<T>(ctx_, maxloc);
+  d64_ = DArr<double>(ctx_, maxloc + 8);
+  if (prm_.local_mixed && std::is_same<T, double>::value) {
+    PL32_ = DArr<float>(ctx_, maxenvT);
+    PR32_ = DArr<float>(ctx_, maxenvT);
+    g32_ = DArr<float>(ctx_, maxloc);
+    y32_ = DArr<float>(ctx_, maxloc);
+    Bx32_ = DArr<float>(ctx_, maxloc);
+    r32_ = DArr<float>(ctx_, maxloc);
+    p32_ = DArr<float>(ctx_, maxloc);
+    Ap32_ = DArr<float>(ctx_, maxloc);
+    z32_ = DArr<float>(ctx_, maxloc);
+    ws32_ = DArr<float>(ctx_, maxws);
+  }
   ctl_ = DArr<int>(ctx_, 4);
   host_ = ctx_->host_pinned;
 
@@ -541,33 +584,35 @@ void Amen<T>::source_proj(int k, bool zl, bool zr, double* out, int ry0, int ry1
 }
 
 template <typename T>
-int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
-  const int n = ncur(k), a0 = acur(k), a1 = acur(k + 1);
-  const int r0 = rx_[k], r1 = rx_[k + 1];
+template <typename U>
+bool Amen<T>::setup_pre(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, DArr<U>& work) {
+  if (!prm_.precond || !bj_fits(r0, n, r1)) return false;
+  work.ensure(ctx_, bj_work_elems(r0, n, r1, a0, a1));
+  bjP_.ensure(ctx_, (size_t)r1 * r0 * n * r0 * n);
+  const bool ok = bj_setup<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, bjP_.p, work.p, work.n, ctl_.p + 2);
+  if (ok) ++precond_solves_;
+  return ok;
+}
+
+// Preconditioned conjugate gradients on B y = g from the given y, to ||g - B y|| <= rtol ||g||.
+// Control flow stays on the device (ctl); the host reads two integers every 8 iterations.
+template <typename T>
+template <typename U>
+int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, U* y,
+                     const U* g, double gnorm, double rtol, const CgBufs<U>& b) {
   const size_t N = (size_t)r0 * n * r1;
-  const T* PL = EL(0, k);
-  const T* PR = ER(0, k);
-  const T* Ak = Acur(k);
   double* prr[2] = {part_.p, part_.p + kReduceBlocks};
   double* prz_b[2] = {part_.p + 2 * kReduceBlocks, part_.p + 3 * kReduceBlocks};
   double* ppap = part_.p + 4 * kReduceBlocks;
   int* ctl = ctl_.p;
-  // block-Jacobi preconditioner of this local system (falls back to plain CG when unusable)
-  bool pre = false;
-  if (prm_.precond && bj_fits(r0, n, r1)) {
-    const size_t need = bj_work_elems(r0, n, r1, a0, a1);
-    bjw_.ensure(ctx_, need);
-    bjP_.ensure(ctx_, (size_t)r1 * r0 * n * r0 * n);
-    pre = bj_setup<T>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, bjP_.p, bjw_.p, bjw_.n, ctl_.p + 2);
-  }
-  T* z = pre ? z_.p : r_.p;
-  double** prz = pre ? prz_b : prr;
+  U* z = b.pre ? b.z : b.r;
+  double** prz = b.pre ? prz_b : prr;
   TN_CHECK_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), ctx_->stream));
-  local_matvec<T>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, Bx_.p, wsT_.p, wsT_.n);
+  local_matvec<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, b.Bx, b.ws, b.wsn);
   count_apply(r0, r1, r0, r1, n, a0, a1);
-  cg_init_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(g, Bx_.p, r_.p, p_.p, N, prr[0]);
+  cg_init_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(g, b.Bx, b.r, b.p, N, prr[0]);
   count_launch(ctx_);
-  if (pre) bj_apply<T>(ctx_, r0, n, r1, bjP_.p, r_.p, z_.p, p_.p, prz[0], nullptr);
+  if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, b.p, prz[0], nullptr);
   const double stop2 = rtol * rtol * gnorm * gnorm;
   int done_it = 0;
   int cur = 0;
@@ -577,20 +622,20 @@ int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
     int chunk = std::min(8, maxit - it);
     for (int c = 0; c < chunk; ++c) {
       const int nx = cur ^ 1;
-      local_matvec<T>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, p_.p, Ap_.p, wsT_.p, wsT_.n, ctl);
+      local_matvec<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, b.p, b.Ap, b.ws, b.wsn, ctl);
       {
-        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 2.0 * N * sizeof(T));
-        cg_dot_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(p_.p, Ap_.p, N, ppap, ctl);
+        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 2.0 * N * sizeof(U));
+        cg_dot_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(b.p, b.Ap, N, ppap, ctl);
       }
       {
-        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 6.0 * N, 6.0 * N * sizeof(T));
-        cg_update1_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(y, r_.p, p_.p, Ap_.p, N, prr[cur], prz[cur], ppap,
+        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 6.0 * N, 6.0 * N * sizeof(U));
+        cg_update1_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(y, b.r, b.p, b.Ap, N, prr[cur], prz[cur], ppap,
                                                                      prr[nx], ctl, stop2);
       }
-      if (pre) bj_apply<T>(ctx_, r0, n, r1, bjP_.p, r_.p, z_.p, nullptr, prz[nx], ctl);
+      if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, nullptr, prz[nx], ctl);
       {
-        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 3.0 * N * sizeof(T));
-        cg_update2_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(p_.p, z, N, prz[nx], prz[cur], ctl);
+        ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 3.0 * N * sizeof(U));
+        cg_update2_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(b.p, z, N, prz[nx], prz[cur], ctl);
       }
       count_launch(ctx_, 3);
       cur = nx;
@@ -601,12 +646,88 @@ int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
     TN_CHECK_CUDA(cudaMemcpyAsync(h, ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx_->stream));
     sync(ctx_);
     done_it = h[1];
-    if (h[0] == 2) throw Error(TNFEM_E_NUMERIC, "local solve: non-positive curvature in conjugate gradients");
+    if (h[0] == 2) {
+      // Loss of positive curvature (rounding in a binary32 solve of an ill-conditioned system):
+      // the iterate of the last completed step is kept and the sweep carries on.
+      ++breakdowns_;
+      if (b.pre && done_it < 2) {
+        // the binary32 block inverses were not positive definite: retry unpreconditioned
+        CgBufs<U> plain = b;
+        plain.pre = false;
+        for (int i = 0; i < done_it; ++i) count_apply(r0, r1, r0, r1, n, a0, a1);
+        return done_it + pcg_run<U>(r0, n, r1, a0, a1, PL, Ak, PR, y, g, gnorm, rtol, plain);
+      }
+      break;
+    }
     if (h[0]) break;
   }
   for (int i = 0; i < done_it; ++i) count_apply(r0, r1, r0, r1, n, a0, a1);
-  if (pre) ++precond_solves_;
   return done_it;
+}
+
+template <typename T>
+int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
+  if (prm_.local_mixed && std::is_same<T, double>::value) return cg_local_mixed(k, y, g, gnorm, rtol);
+  const int n = ncur(k), a0 = acur(k), a1 = acur(k + 1);
+  const int r0 = rx_[k], r1 = rx_[k + 1];
+  const T* PL = EL(0, k);
+  const T* PR = ER(0, k);
+  const T* Ak = Acur(k);
+  const bool pre = setup_pre<T>(r0, n, r1, a0, a1, PL, Ak, PR, bjw_);
+  CgBufs<T> b{Bx_.p, r_.p, p_.p, Ap_.p, z_.p, wsT_.p, wsT_.n, pre};
+  return pcg_run<T>(r0, n, r1, a0, a1, PL, Ak, PR, y, g, gnorm, rtol, b);
+}
+
+// Binary64 sweep, binary32 local solves: iterative refinement of the local system against its
+// binary64 residual.  Each step solves B d = r / ||r|| by binary32 preconditioned CG (interfaces
+// and operator core rounded to binary32) and updates y += ||r|| d in binary64, until the binary64
+// local residual meets rtol.
+template <typename T>
+int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) {
+  if constexpr (!std::is_same<T, double>::value) {
+    (void)k; (void)y; (void)g; (void)gnorm; (void)rtol;
+    throw Error(TNFEM_E_INVALID, "binary32 local solves need a binary64 sweep");
+  } else {
+    const int n = ncur(k), a0 = acur(k), a1 = acur(k + 1);
+    const int r0 = rx_[k], r1 = rx_[k + 1];
+    const size_t N = (size_t)r0 * n * r1;
+    const double* PL = EL(0, k);
+    const double* PR = ER(0, k);
+    const double* Ak = Acur(k);
+    convert_d2f(ctx_, PL32_.p, PL, (size_t)r0 * a0 * r0);
+    convert_d2f(ctx_, PR32_.p, PR, (size_t)r1 * a1 * r1);
+    const float* A32 = A_->p32[o_][k];
+    const bool pre = setup_pre<float>(r0, n, r1, a0, a1, PL32_.p, A32, PR32_.p, bjw32_);
+    CgBufs<float> b{Bx32_.p, r32_.p, p32_.p, Ap32_.p, z32_.p, ws32_.p, ws32_.n, pre};
+    int iters = 0;
+    double prev = 0.0;
+    for (int step = 0; step < 12; ++step) {
+      // binary64 residual r = g - B y
+      local_matvec<double>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, Bx_.p, wsT_.p, wsT_.n);
+      count_apply(r0, r1, r0, r1, n, a0, a1);
+      diff_kernel<double><<<kReduceBlocks, RT, 0, ctx_->stream>>>(r_.p, g, Bx_.p, N, part_.p + 5 * kReduceBlocks);
+      sum_partials_kernel<<<1, RT, 0, ctx_->stream>>>(part_.p + 5 * kReduceBlocks, d64_.p + N);
+      count_launch(ctx_, 2);
+      double rn2 = 0;
+      TN_CHECK_CUDA(cudaMemcpyAsync(&rn2, d64_.p + N, sizeof(double), cudaMemcpyDeviceToHost, ctx_->stream));
+      sync(ctx_);
+      const double rn = std::sqrt(rn2);
+      if (!(rn > rtol * gnorm)) break;
+      if (step > 0 && !(rn < 0.5 * prev)) break;  // stagnation: binary32 cannot reduce it further
+      prev = rn;
+      ++local_refines_;
+      // d solves B d = r / ||r|| in binary32 to the reduction still needed (not below 1e-6)
+      scale_to_float_kernel<<<nblk((long long)N), RT, 0, ctx_->stream>>>(g32_.p, r_.p, 1.0 / rn, N);
+      count_launch(ctx_);
+      fill<float>(ctx_, y32_.p, 0.0f, N);
+      const double need = rtol * gnorm / rn;
+      iters += pcg_run<float>(r0, n, r1, a0, a1, PL32_.p, A32, PR32_.p, y32_.p, g32_.p, 1.0,
+                              std::max(1e-6, 0.5 * need), b);
+      add_scaled_float_kernel<<<nblk((long long)N), RT, 0, ctx_->stream>>>(y, y32_.p, rn, N);
+      count_launch(ctx_);
+    }
+    return iters;
+  }
 }
 
 template <typename T>

@@ -23,6 +23,7 @@ struct AmenParams {
   int local_maxit = 500;    // conjugate-gradient iterations per local solve
   double resid_damp = 2.0;  // local solves stop at tol / resid_damp
   bool precond = true;      // block-Jacobi preconditioned conjugate gradients for the local solves
+  bool local_mixed = false; // binary64 sweep with binary32 local solves refined in binary64
   uint64_t seed = 0;
   bool verbose = false;
 };

@@ -341,12 +341,14 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
     }
     TN_REQUIRE(opts->tol > 0 && opts->rank_cap >= 1 && opts->kickrank >= 0 && opts->max_sweeps >= 1,
                "solve options out of range");
-    TN_REQUIRE(opts->precision == TNFEM_FP64 || opts->precision == TNFEM_MIXED, "precision");
+    TN_REQUIRE(opts->precision == TNFEM_FP64 || opts->precision == TNFEM_MIXED ||
+                   opts->precision == TNFEM_MIXED_LOCAL,
+               "precision");
     sync(ctx);
     auto t0 = std::chrono::steady_clock::now();
     tnfem_tt* res = nullptr;
     if (info) memset(info, 0, sizeof(*info));
-    if (opts->precision == TNFEM_FP64) {
+    if (opts->precision == TNFEM_FP64 || opts->precision == TNFEM_MIXED_LOCAL) {
       AmenParams p;
       p.tol = opts->tol;
       p.rmax = opts->rank_cap;
@@ -355,6 +357,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
       p.local_maxit = opts->local_maxit > 0 ? opts->local_maxit : 500;
       p.seed = opts->seed;
       p.precond = opts->no_precond == 0;
+      p.local_mixed = opts->precision == TNFEM_MIXED_LOCAL;
       p.verbose = getenv("TNFEM_VERBOSE") != nullptr;
       AmenStats s;
       res = amen_solve(ctx, A, {AmenSource{f, false, 1.0}}, p, x0, false, s);

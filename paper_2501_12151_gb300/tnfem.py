@@ -173,7 +173,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.rank_cap = int(o.rank_cap)
     co.kickrank = int(o.kickrank)
     co.max_sweeps = int(o.max_sweeps)
-    co.precision = 1 if o.precision == "mixed" else 0
+    co.precision = {"fp64": 0, "mixed": 1, "mixed-local": 2}[o.precision]
     co.refine_tol = float(o.refine_tol)
     co.max_refine = int(o.max_refine)
     co.seed = int(o.seed)

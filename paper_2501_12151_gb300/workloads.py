@@ -83,7 +83,7 @@ class SolveOpts:
     rank_cap: int = 16
     kickrank: int = 4
     max_sweeps: int = 40
-    precision: str = "fp64"   # "fp64" or "mixed"
+    precision: str = "fp64"   # "fp64", "mixed" (outer TT-residual refinement) or "mixed-local"
     refine_tol: float = 1e-6
     max_refine: int = 20
     seed: int = 0

@@ -98,6 +98,37 @@ def test_fp64_rank_capped_config_matches_oracle_amen(ctx):
     assert err_gpu <= 2.0 * err_orc + 1e-9, (err_gpu, err_orc)
 
 
+@pytest.mark.parametrize("case", ["manufactured5", "steel6"])
+def test_mixed_local_solve_matches_galerkin(ctx, case):
+    """Binary32 local solves refined against binary64 local residuals reach the binary64 bar."""
+    if case == "manufactured5":
+        pr = W.manufactured_2d(levels=5, rank_cap=64, tol=1e-11)
+    else:
+        pr = W.steel_plate_2d(levels=6, rank_cap=64, tol=1e-11)
+    pr.opts.precision = "mixed-local"
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    u, info = ctx.solve(A, f, pr.opts)
+    err = _energy_err(Abc, tt.tt_full(u.cores()), uh, pr.grid)
+    assert info["converged"] == 1, info
+    assert err <= 1e-8, (err, info)
+
+
+def test_unpreconditioned_local_solves_agree(ctx):
+    """Plain CG and block-Jacobi PCG local solves reach the same Galerkin solution."""
+    pr = W.manufactured_2d(levels=4, rank_cap=64, tol=1e-11)
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    errs = []
+    for pc in (True, False):
+        pr.opts.precond = pc
+        u, info = ctx.solve(A, f, pr.opts)
+        errs.append(_energy_err(Abc, tt.tt_full(u.cores()), uh, pr.grid))
+    assert max(errs) <= 1e-8, errs
+
+
 def test_mixed_solve_reaches_1e6(ctx):
     pr = W.steel_plate_2d(levels=6, rank_cap=64, tol=1e-10, precision="mixed")
     pr.opts.refine_tol = 1e-7
