@@ -261,6 +261,27 @@ tnfem_status tnfem_op_local_matvec(tnfem_ctx* ctx, int r0, int n, int r1, int a0
 tnfem_status tnfem_op_env_left(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx1, int n, int a0,
                                int a1, const double* Phi, const double* y, const double* A,
                                const double* x, double* out);
+/* Local matvec of tnfem_op_local_matvec for callers that cannot allocate device memory (a
+ * function running inside a CUDA stream capture that must not grow the memory pool, a host
+ * framework that owns the device allocator, a real-time loop that must not block on cudaMalloc).
+ * This entry point has no counterpart in the paper; it is the same contraction with its
+ * intermediates taken from a static device array of TNFEM_NOALLOC_SCRATCH_DOUBLES binary64
+ * elements (32 MiB), which every GPU that loads the library holds until the process exits.
+ *  - stream: cudaStream_t (NULL: legacy default stream); the work is enqueued on it and the call
+ *    returns without synchronising.  Device pointers and layouts as for tnfem_op_local_matvec; no
+ *    context is needed, the current device is used.
+ *  - Limit: a0*n*n*a1 + r0*a0*n*r1 + r0*n*a1*r1 + 1024 <= TNFEM_NOALLOC_SCRATCH_DOUBLES, else
+ *    TNFEM_E_INVALID (as for null pointers or sizes < 1); TNFEM_E_CUDA if the device or the
+ *    array's address cannot be obtained.
+ *  - No cudaMalloc / cudaFree or other allocating routine is called.  The first call on each
+ *    device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ *    make that first call before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU race and must be serialised by the
+ *    caller.  The array keeps the last call's contents; nothing in it needs to start at zero. */
+#define TNFEM_NOALLOC_SCRATCH_DOUBLES (1ll << 22)
+tnfem_status tnfem_op_local_matvec_noalloc(void* stream, int r0, int n, int r1, int a0, int a1,
+                                           const double* PhiL, const double* A, const double* PhiR,
+                                           const double* x, double* y);
 /* Reduced Householder QR of an m x n row-major matrix: Q [m][k], R [k][n], k = min(m, n),
  * diag(R) >= 0 is not enforced (Householder signs). */
 tnfem_status tnfem_op_qr(tnfem_ctx* ctx, int m, int n, const double* Ain, double* Q, double* R);

@@ -109,6 +109,7 @@ _sig("tnfem_op_local_matvec", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, 
 _sig("tnfem_op_env_left", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_qr", _i, [_vp, _i, _i, _vp, _vp, _vp])
 _sig("tnfem_op_svd", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp])
+_sig("tnfem_op_local_matvec_noalloc", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_profile_start", _i, [_vp, _i])
 _sig("tnfem_profile_read", _i, [_vp, _i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pd, _pd, _pd])
 
@@ -186,6 +187,12 @@ def _check(st: int, ctx=None):
     if st != 0:
         msg = lib.tnfem_last_error(ctx).decode() if ctx else ""
         raise TnfemError(st, msg)
+
+
+def op_local_matvec_noalloc(stream: int, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y):
+    """Local matvec on device pointers with the library's static scratch array (allocates
+    nothing; enqueued on ``stream`` without synchronising)."""
+    _check(lib.tnfem_op_local_matvec_noalloc(C.c_void_p(stream), r0, n, r1, a0, a1, PhiL, A, PhiR, x, y))
 
 
 # ---------------------------------------------------------------------------------------
