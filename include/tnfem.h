@@ -120,8 +120,10 @@ typedef struct {
 
 /* ---- context ------------------------------------------------------------------------------ */
 
-/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t (may be NULL for the
- * legacy default stream); all device work of this context is enqueued on it.  The optional
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t; all device work of this
+ * context is enqueued on it.  With NULL the context creates its own blocking stream (ordered
+ * with the legacy default stream in both directions, like NULL itself, but capturable into the
+ * CUDA graphs the sweep replays); tnfem_set_stream(ctx, NULL) returns to that stream.  The optional
  * allocator callbacks route every device allocation of the context (e.g. into a framework's
  * caching allocator); when alloc_fn is NULL the library calls cudaMalloc/cudaFree itself. */
 typedef void* (*tnfem_alloc_fn)(size_t bytes, void* user);

@@ -203,6 +203,70 @@ void convert_any(tnfem_ctx* ctx, D* dst, const S* src, size_t n) {
 
 // ------------------------------------------------------------------------------------------------
 
+// A captured sequence of launches on the context's stream, replayed as one CUDA graph launch.
+// Launch and profiling counters of the captured kernels are credited on every replay.
+struct ChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  long long seen[TNFEM_PROF_CLASSES] = {};
+  ChunkGraph() = default;
+  ChunkGraph(const ChunkGraph&) = delete;
+  ChunkGraph& operator=(const ChunkGraph&) = delete;
+  ~ChunkGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  template <typename F>
+  void capture(tnfem_ctx* ctx, F&& body) {
+    const long long l0 = ctx->launches;
+    long long s0[TNFEM_PROF_CLASSES];
+    for (int c = 0; c < TNFEM_PROF_CLASSES; ++c) s0[c] = ctx->prof_seen[c];
+    TN_CHECK_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    cudaGraph_t g = nullptr;
+    try {
+      body();
+    } catch (...) {
+      ctx->capturing = false;
+      cudaStreamEndCapture(ctx->stream, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    ctx->capturing = false;
+    TN_CHECK_CUDA(cudaStreamEndCapture(ctx->stream, &g));
+    kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    for (int c = 0; c < TNFEM_PROF_CLASSES; ++c) {
+      seen[c] = ctx->prof_seen[c] - s0[c];
+      ctx->prof_seen[c] = s0[c];
+    }
+    bool ok = false;
+    if (exec) {
+      cudaGraphExecUpdateResultInfo info;
+      ok = cudaGraphExecUpdate(exec, g, &info) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+      }
+    }
+    if (!ok) {
+      cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+      if (e != cudaSuccess) {
+        exec = nullptr;
+        cudaGraphDestroy(g);
+        throw Error(TNFEM_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    cudaGraphDestroy(g);
+  }
+  void launch(tnfem_ctx* ctx) {
+    TN_CHECK_CUDA(cudaGraphLaunch(exec, ctx->stream));
+    ctx->launches += kernels;
+    for (int c = 0; c < TNFEM_PROF_CLASSES; ++c) ctx->prof_seen[c] += seen[c];
+  }
+};
+
 template <typename T>
 class Amen {
  public:
@@ -300,6 +364,7 @@ class Amen {
   DArr<double> d64_;
   long long local_refines_ = 0;
   long long breakdowns_ = 0;
+  ChunkGraph graph_[2];  // conjugate-gradient chunk graphs, binary32 / binary64
   double* host_ = nullptr;
   double flops_ = 0.0;
   long long iters_ = 0;
@@ -595,7 +660,10 @@ bool Amen<T>::setup_pre(int r0, int n, int r1, int a0, int a1, const U* PL, cons
 }
 
 // Preconditioned conjugate gradients on B y = g from the given y, to ||g - B y|| <= rtol ||g||.
-// Control flow stays on the device (ctl); the host reads two integers every 8 iterations.
+// Control flow stays on the device (ctl); the host reads two integers after every chunk of 8
+// iterations.  On a capturable stream the chunk is captured once per local solve into a CUDA
+// graph (updated in place when the previous solve's graph has the same topology) and replayed,
+// so the host issues one graph launch instead of ~60 kernel launches per chunk.
 template <typename T>
 template <typename U>
 int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, U* y,
@@ -614,13 +682,10 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
   count_launch(ctx_);
   if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, b.p, prz[0], nullptr);
   const double stop2 = rtol * rtol * gnorm * gnorm;
-  int done_it = 0;
-  int cur = 0;
-  const int maxit = prm_.local_maxit;
-  int it = 0;
-  while (it < maxit) {
-    int chunk = std::min(8, maxit - it);
-    for (int c = 0; c < chunk; ++c) {
+  constexpr int kChunk = 8;  // even: the partial-sum buffers are back at index 0 after a chunk
+  auto chunk = [&]() {
+    int cur = 0;
+    for (int c = 0; c < kChunk; ++c) {
       const int nx = cur ^ 1;
       local_matvec<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, b.p, b.Ap, b.ws, b.wsn, ctl);
       {
@@ -640,7 +705,17 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
       count_launch(ctx_, 3);
       cur = nx;
     }
-    it += chunk;
+  };
+  ChunkGraph& cgph = graph_[sizeof(U) == 8 ? 1 : 0];
+  const bool use_graph = prm_.graphs && ctx_->stream != nullptr;
+  if (use_graph) cgph.capture(ctx_, chunk);
+  int done_it = 0;
+  const int maxit = prm_.local_maxit;
+  int it = 0;
+  while (it < maxit) {
+    if (use_graph) cgph.launch(ctx_);
+    else chunk();
+    it += kChunk;
     check_launch(ctx_, "cg");
     int h[2];
     TN_CHECK_CUDA(cudaMemcpyAsync(h, ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx_->stream));

@@ -24,6 +24,7 @@ struct AmenParams {
   double resid_damp = 2.0;  // local solves stop at tol / resid_damp
   bool precond = true;      // block-Jacobi preconditioned conjugate gradients for the local solves
   bool local_mixed = false; // binary64 sweep with binary32 local solves refined in binary64
+  bool graphs = true;       // replay the conjugate-gradient chunks as CUDA graphs
   uint64_t seed = 0;
   bool verbose = false;
 };

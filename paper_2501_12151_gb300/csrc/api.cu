@@ -230,6 +230,12 @@ tnfem_status tnfem_create(int device, void* stream, tnfem_alloc_fn alloc_fn, tnf
     TN_CHECK_CUDA(cudaSetDevice(device));
     ctx->device = device;
     ctx->stream = static_cast<cudaStream_t>(stream);
+    if (!ctx->stream) {
+      // a private stream that synchronises with the legacy default stream like NULL does, and
+      // that (unlike NULL) can be captured into CUDA graphs
+      TN_CHECK_CUDA(cudaStreamCreate(&ctx->stream));
+      ctx->own_stream = true;
+    }
     ctx->alloc_fn = alloc_fn;
     ctx->free_fn = free_fn;
     ctx->user = user;
@@ -238,6 +244,7 @@ tnfem_status tnfem_create(int device, void* stream, tnfem_alloc_fn alloc_fn, tnf
   });
   if (st != TNFEM_OK) {
     if (ctx->scratch) dfree(ctx, ctx->scratch);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return st;
   }
@@ -250,6 +257,7 @@ void tnfem_destroy(tnfem_ctx* ctx) {
   prof_release(ctx);
   if (ctx->scratch) dfree(ctx, ctx->scratch);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
 
@@ -257,6 +265,19 @@ const char* tnfem_last_error(const tnfem_ctx* ctx) { return ctx ? ctx->err.c_str
 
 tnfem_status tnfem_set_stream(tnfem_ctx* ctx, void* stream) {
   if (!ctx) return TNFEM_E_INVALID;
+  if (!stream) {
+    if (!ctx->own_stream) {
+      if (cudaStreamCreate(&ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "cudaStreamCreate failed";
+        return TNFEM_E_CUDA;
+      }
+      ctx->own_stream = true;
+    }
+    return TNFEM_OK;
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  ctx->own_stream = false;
   ctx->stream = static_cast<cudaStream_t>(stream);
   return TNFEM_OK;
 }

@@ -56,6 +56,8 @@ struct tnfem_ctx {
     int cls;
     double flops, bytes;
   };
+  bool capturing = false;  // launches are being captured into a graph
+  bool own_stream = false; // `stream` was created by the context (caller passed NULL)
   int prof_every = 0;
   long long prof_seen[TNFEM_PROF_CLASSES] = {};
   long long prof_sampled[TNFEM_PROF_CLASSES] = {};

@@ -24,6 +24,11 @@ cudaEvent_t take_event(tnfem_ctx* ctx) {
 
 ProfScope::ProfScope(tnfem_ctx* c, int cls, double flops, double bytes) : ctx(c) {
   if (ctx->prof_every <= 0 || cls < 0 || cls >= TNFEM_PROF_CLASSES) return;
+  // launches captured into a graph are credited per replay by the graph; not sampled here
+  if (ctx->capturing) {
+    ctx->prof_seen[cls]++;
+    return;
+  }
   long long seen = ctx->prof_seen[cls]++;
   if (seen % ctx->prof_every != 0) return;
   tnfem_ctx::ProfEv ev{take_event(ctx), take_event(ctx), cls, flops, bytes};
