@@ -52,10 +52,11 @@ def measured_peaks():
         return {}
 
 
-def workload(levels: int, rank_cap: int, precision: str):
+def workload(levels: int, rank_cap: int, precision: str, tensor_cores: bool = False):
     from paper_2501_12151_gb300 import workloads as W
     pr = W.steel_plate_2d(levels=levels, rank_cap=rank_cap, tol=1e-9, precision=precision)
     pr.opts.refine_tol = 1e-6
+    pr.opts.tensor_cores = tensor_cores
     return pr
 
 
@@ -190,10 +191,12 @@ def run_ours(args):
         raise SystemExit("bench.py: no CUDA device (the tnfem library has no CPU path)")
     torch.cuda.set_device(local)
     from paper_2501_12151_gb300 import tnfem
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: capturable into the sweep's CUDA graphs, and the one the events time
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = tnfem.Context(local, stream=stream.cuda_stream, torch_alloc=True)
 
-    pr = workload(args.levels, args.rank_cap, args.precision)
+    pr = workload(args.levels, args.rank_cap, args.precision, args.tensor_cores)
     A = ctx.stiffness(pr.grid, pr.material)
     f = ctx.load(pr.grid, pr.material, pr.loads)
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
@@ -331,6 +334,7 @@ def run_ours(args):
                                f"({2 * 4 ** args.levels} DOF), QTT {args.levels} levels, rank cap {args.rank_cap}, "
                                f"{args.precision}, rel. energy err target 1e-6",
                    "levels": args.levels, "rank_cap": args.rank_cap, "precision": args.precision,
+                   "tensor_cores": bool(args.tensor_cores),
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)"},
         "accuracy": {"energy_err_est": last["energy_err_est"], "refines": last["refines"], "sweeps": last["sweeps"],
                      "max_rank": last["max_rank"], "local_iters": last["local_iters"],
@@ -399,6 +403,7 @@ def main(argv=None):
     ap.add_argument("--levels", type=int, default=10)
     ap.add_argument("--rank-cap", type=int, default=64)
     ap.add_argument("--precision", choices=["mixed", "mixed-local", "fp64"], default="mixed")
+    ap.add_argument("--tensor-cores", action="store_true", help="binary32 contractions on tcgen05")
     ap.add_argument("--prof-every", type=int, default=8, help="time every n-th launch of each kernel class")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-sweeps", type=int, default=3)

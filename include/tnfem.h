@@ -102,6 +102,8 @@ typedef struct {
   uint64_t seed;       /* seed of the counter-based generator for the start guess / enrichment */
   int local_maxit;     /* cap on conjugate-gradient iterations per local solve */
   int no_precond;      /* 0: block-Jacobi preconditioned local solves (default); 1: plain CG */
+  int tensor_cores;    /* MIXED / MIXED_LOCAL: 1 runs the binary32 contractions on the tcgen05
+                          tensor cores (three-term TF32 split), 0 on CUDA-core FMA */
 } tnfem_solve_opts;
 
 typedef struct {
@@ -284,6 +286,19 @@ tnfem_status tnfem_op_env_left(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx
 tnfem_status tnfem_op_local_matvec_noalloc(void* stream, int r0, int n, int r1, int a0, int a1,
                                            const double* PhiL, const double* A, const double* PhiR,
                                            const double* x, double* y);
+/* Binary32 building blocks of the mixed-precision local solves (parity tests of both engines).
+ * engine 0: CUDA-core FMA; engine 1: tcgen05 tensor cores, kind::tf32 with the three-term split
+ * a b = a_hi b_hi + a_hi b_lo + a_lo b_hi (binary32-level accuracy from TF32 products).
+ * tnfem_op_gemm_f32: C(b,m,n) = alpha sum_k A(b,m,k) B(b,k,n) + beta C(b,m,n) with element
+ * (b,m,k) of A at A[b*sAb + m*sAm + k*sAk] (likewise B and C); every pointer is a device pointer to
+ * binary32.  tnfem_op_local_matvec_f32: the contraction of tnfem_op_local_matvec in binary32. */
+tnfem_status tnfem_op_gemm_f32(tnfem_ctx* ctx, int engine, int M, int N, int K, int batch, long long sAm,
+                               long long sAk, long long sAb, long long sBk, long long sBn, long long sBb,
+                               long long sCm, long long sCn, long long sCb, float alpha, const float* A,
+                               const float* B, float beta, float* C);
+tnfem_status tnfem_op_local_matvec_f32(tnfem_ctx* ctx, int engine, int r0, int n, int r1, int a0, int a1,
+                                       const float* PhiL, const float* A, const float* PhiR, const float* x,
+                                       float* y);
 /* Reduced Householder QR of an m x n row-major matrix: Q [m][k], R [k][n], k = min(m, n),
  * diag(R) >= 0 is not enforced (Householder signs). */
 tnfem_status tnfem_op_qr(tnfem_ctx* ctx, int m, int n, const double* Ain, double* Q, double* R);

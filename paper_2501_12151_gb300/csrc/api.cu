@@ -13,6 +13,14 @@ using namespace tnfem;
 
 namespace {
 
+// sets the binary32 GEMM engine for the duration of one call
+struct EngineScope {
+  tnfem_ctx* ctx;
+  bool saved;
+  EngineScope(tnfem_ctx* c, int engine) : ctx(c), saved(c->tensor_cores) { c->tensor_cores = engine == 1; }
+  ~EngineScope() { ctx->tensor_cores = saved; }
+};
+
 template <typename F>
 tnfem_status guard(tnfem_ctx* ctx, F&& f) {
   try {
@@ -240,6 +248,8 @@ tnfem_status tnfem_create(int device, void* stream, tnfem_alloc_fn alloc_fn, tnf
     ctx->free_fn = free_fn;
     ctx->user = user;
     ctx->scratch = static_cast<double*>(dalloc(ctx, kScratchDoubles * sizeof(double)));
+    TN_CHECK_CUDA(cudaMemsetAsync(ctx->scratch, 0, kScratchDoubles * sizeof(double), ctx->stream));
+    TN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
     TN_CHECK_CUDA(cudaMallocHost(&ctx->host_pinned, 4096));
   });
   if (st != TNFEM_OK) {
@@ -366,6 +376,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
                    opts->precision == TNFEM_MIXED_LOCAL,
                "precision");
     sync(ctx);
+    EngineScope es(ctx, opts->tensor_cores ? 1 : 0);
     auto t0 = std::chrono::steady_clock::now();
     tnfem_tt* res = nullptr;
     if (info) memset(info, 0, sizeof(*info));
@@ -687,6 +698,41 @@ tnfem_status tnfem_op_local_matvec(tnfem_ctx* ctx, int r0, int n, int r1, int a0
     transpose4_mid<double>(ctx, Ap.p, A, a0, n, n, a1);
     DArr<double> ws(ctx, local_ws_elems(r0, n, r1, a0, a1));
     local_matvec<double>(ctx, r0, n, r1, a0, a1, PhiL, Ap.p, PhiR, x, y, ws.p, ws.n);
+    sync(ctx);
+  });
+}
+
+tnfem_status tnfem_op_gemm_f32(tnfem_ctx* ctx, int engine, int M, int N, int K, int batch, long long sAm,
+                               long long sAk, long long sAb, long long sBk, long long sBn, long long sBb,
+                               long long sCm, long long sCn, long long sCb, float alpha, const float* A,
+                               const float* B, float beta, float* C) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    TN_REQUIRE(A && B && C, "null pointer");
+    TN_REQUIRE(engine == 0 || engine == 1, "engine must be 0 (CUDA cores) or 1 (tensor cores)");
+    TN_REQUIRE(M >= 1 && N >= 1 && K >= 1 && batch >= 1, "sizes must be positive");
+    EngineScope es(ctx, engine);
+    GemmDesc g{M, N, K, batch, sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb};
+    const size_t work = (size_t)64 * batch * M * N;
+    DArr<float> w(ctx, std::min<size_t>(work, (size_t)1 << 26));
+    gemm<float>(ctx, g, alpha, A, B, beta, C, w.p, w.n);
+    sync(ctx);
+  });
+}
+
+tnfem_status tnfem_op_local_matvec_f32(tnfem_ctx* ctx, int engine, int r0, int n, int r1, int a0, int a1,
+                                       const float* PhiL, const float* A, const float* PhiR, const float* x,
+                                       float* y) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    TN_REQUIRE(PhiL && A && PhiR && x && y, "null pointer");
+    TN_REQUIRE(engine == 0 || engine == 1, "engine must be 0 (CUDA cores) or 1 (tensor cores)");
+    TN_REQUIRE(r0 >= 1 && r1 >= 1 && n >= 1 && a0 >= 1 && a1 >= 1, "sizes must be positive");
+    EngineScope es(ctx, engine);
+    DArr<float> Ap(ctx, (size_t)a0 * n * n * a1);
+    transpose4_mid<float>(ctx, Ap.p, A, a0, n, n, a1);
+    DArr<float> ws(ctx, local_ws_elems(r0, n, r1, a0, a1));
+    local_matvec<float>(ctx, r0, n, r1, a0, a1, PhiL, Ap.p, PhiR, x, y, ws.p, ws.n);
     sync(ctx);
   });
 }

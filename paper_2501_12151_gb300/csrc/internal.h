@@ -57,6 +57,7 @@ struct tnfem_ctx {
     double flops, bytes;
   };
   bool capturing = false;  // launches are being captured into a graph
+  bool tensor_cores = false;  // binary32 GEMMs on tcgen05 (three-term TF32) instead of CUDA cores
   bool own_stream = false; // `stream` was created by the context (caller passed NULL)
   int prof_every = 0;
   long long prof_seen[TNFEM_PROF_CLASSES] = {};
@@ -128,6 +129,10 @@ template <typename T>
 void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T beta, T* C,
           T* work = nullptr, size_t work_elems = 0, const int* skip = nullptr);
 
+// C = alpha * sum over splits of work + beta * C (split-K epilogue, work [split][batch][M][N])
+template <typename T>
+void splitk_reduce(tnfem_ctx* ctx, const GemmDesc& g, T alpha, T beta, T* C, const T* work, int splits,
+                   const int* skip);
 template <typename T> void fill(tnfem_ctx* ctx, T* x, T v, size_t n);
 template <typename T> void copy(tnfem_ctx* ctx, T* dst, const T* src, size_t n);
 template <typename T> void axpby(tnfem_ctx* ctx, T* y, T a, const T* x, T b, size_t n);  // y = a x + b y

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tc_gemm.h"
 
 namespace tnfem {
 
@@ -274,6 +275,12 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
     }
     return;
   }
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->tensor_cores && tc_gemm_supported(g)) {
+      tc_gemm(ctx, g, alpha, A, B, beta, C, work, work_elems, skip);
+      return;
+    }
+  }
   int tiles_m = (g.M + BM - 1) / BM, tiles_n = (g.N + BN - 1) / BN;
   long long tiles = (long long)tiles_m * tiles_n * g.batch;
   int splits = 1;
@@ -304,6 +311,15 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
     count_launch(ctx);
   }
   check_launch(ctx, "gemm");
+}
+
+template <typename T>
+void splitk_reduce(tnfem_ctx* ctx, const GemmDesc& g, T alpha, T beta, T* C, const T* work, int splits,
+                   const int* skip) {
+  long long total = (long long)g.batch * g.M * g.N;
+  ProfScope ps(ctx, TNFEM_PROF_OTHER, (double)total * splits, (double)total * (splits + 1) * sizeof(T));
+  splitk_reduce_kernel<T><<<grid_for(total), 256, 0, ctx->stream>>>(g, alpha, beta, C, work, splits, skip);
+  count_launch(ctx);
 }
 
 template <typename T> void fill(tnfem_ctx* ctx, T* x, T v, size_t n) {
@@ -389,6 +405,10 @@ template <typename T> void transpose2(tnfem_ctx* ctx, T* out, const T* in, int m
   count_launch(ctx);
   check_launch(ctx, "transpose2");
 }
+
+template void splitk_reduce<double>(tnfem_ctx*, const GemmDesc&, double, double, double*, const double*, int,
+                                    const int*);
+template void splitk_reduce<float>(tnfem_ctx*, const GemmDesc&, float, float, float*, const float*, int, const int*);
 
 #define TN_INST(T)                                                                              \
   template void gemm<T>(tnfem_ctx*, const GemmDesc&, T, const T*, const T*, T, T*, T*, size_t,    \

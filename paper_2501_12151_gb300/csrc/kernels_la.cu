@@ -13,6 +13,7 @@ namespace tnfem {
 namespace {
 
 constexpr int LT = 1024;
+constexpr size_t kSvdSmemMax = 200 * 1024;  // working copies of the Jacobi SVD up to this size stay on chip
 
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
@@ -127,11 +128,16 @@ __global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A,
 }
 
 // One-sided Jacobi SVD.  G: m x n column-major work copy of A, V: n x n column-major.
+// With use_smem the working copies G, V and sig live in dynamic shared memory (when they fit);
+// otherwise in the global work buffers passed in.
 template <typename T>
 __global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
                                                  T* __restrict__ S, T* __restrict__ Vt,
-                                                 T* __restrict__ G, T* __restrict__ V,
-                                                 T* __restrict__ sig, int max_sweeps) {
+                                                 T* Gg, T* Vg, T* sigg, int max_sweeps, int use_smem) {
+  extern __shared__ __align__(16) unsigned char svd_smem[];
+  T* G = use_smem ? reinterpret_cast<T*>(svd_smem) : Gg;
+  T* V = use_smem ? G + (size_t)m * n : Vg;
+  T* sig = use_smem ? V + (size_t)n * n : sigg;
   __shared__ int s_rot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (long long t = threadIdx.x; t < (long long)m * n; t += blockDim.x) {
@@ -249,7 +255,16 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   T* V = G + (size_t)m * n;
   T* sig = V + (size_t)n * n;
   ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
-  svd_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, U, S, Vt, G, V, sig, sizeof(T) == 8 ? 60 : 40);
+  const size_t smem = ((size_t)m * n + (size_t)n * n + n) * sizeof(T);
+  const int use_smem = smem <= kSvdSmemMax ? 1 : 0;
+  static unsigned long long attr_set = 0;  // one bit per device
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (use_smem && !(attr_set & bit)) {
+    TN_CHECK_CUDA(cudaFuncSetAttribute(svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSvdSmemMax));
+    attr_set |= bit;
+  }
+  svd_kernel<T><<<1, LT, use_smem ? smem : 0, ctx->stream>>>(m, n, A, U, S, Vt, G, V, sig, sizeof(T) == 8 ? 60 : 40,
+                                                            use_smem);
   count_launch(ctx);
   check_launch(ctx, "svd");
 }

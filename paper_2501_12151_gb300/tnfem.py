@@ -48,7 +48,8 @@ class CLoad(C.Structure):
 class COpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("rank_cap", C.c_int), ("kickrank", C.c_int), ("max_sweeps", C.c_int),
                 ("precision", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int),
-                ("seed", C.c_uint64), ("local_maxit", C.c_int), ("no_precond", C.c_int)]
+                ("seed", C.c_uint64), ("local_maxit", C.c_int), ("no_precond", C.c_int),
+                ("tensor_cores", C.c_int)]
 
 
 class CInfo(C.Structure):
@@ -110,6 +111,9 @@ _sig("tnfem_op_env_left", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _
 _sig("tnfem_op_qr", _i, [_vp, _i, _i, _vp, _vp, _vp])
 _sig("tnfem_op_svd", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_local_matvec_noalloc", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
+_ll = C.c_longlong
+_sig("tnfem_op_gemm_f32", _i, [_vp, _i, _i, _i, _i, _i] + [_ll] * 9 + [C.c_float, _vp, _vp, C.c_float, _vp])
+_sig("tnfem_op_local_matvec_f32", _i, [_vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_profile_start", _i, [_vp, _i])
 _sig("tnfem_profile_read", _i, [_vp, _i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pd, _pd, _pd])
 
@@ -180,6 +184,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.seed = int(o.seed)
     co.local_maxit = int(local_maxit)
     co.no_precond = 0 if getattr(o, "precond", True) else 1
+    co.tensor_cores = 1 if getattr(o, "tensor_cores", False) else 0
     return co
 
 
@@ -357,6 +362,12 @@ class Context:
 
     def op_env_left(self, ry0, ry1, rx0, rx1, n, a0, a1, Phi, y, A, x, out):
         self.check(lib.tnfem_op_env_left(self.h, ry0, ry1, rx0, rx1, n, a0, a1, Phi, y, A, x, out))
+
+    def op_gemm_f32(self, engine, M, N, K, batch, strides, alpha, A, B, beta, Cp):
+        self.check(lib.tnfem_op_gemm_f32(self.h, engine, M, N, K, batch, *strides, alpha, A, B, beta, Cp))
+
+    def op_local_matvec_f32(self, engine, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y):
+        self.check(lib.tnfem_op_local_matvec_f32(self.h, engine, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y))
 
     def op_qr(self, m, n, A, Q, R):
         self.check(lib.tnfem_op_qr(self.h, m, n, A, Q, R))

@@ -88,6 +88,7 @@ class SolveOpts:
     max_refine: int = 20
     seed: int = 0
     precond: bool = True      # block-Jacobi preconditioned local solves
+    tensor_cores: bool = False  # binary32 contractions on the tcgen05 tensor cores
 
 
 @dataclass
