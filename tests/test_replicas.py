@@ -51,6 +51,6 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch):
     import bench
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
-    ns = type("A", (), {"levels": 3, "rank_cap": 8, "steps": 1, "warmup": 0, "cpu_sweeps": 1,
-                        "ref_full_sweeps": 2, "precision": "fp64"})()
+    ns = type("A", (), {"levels": 3, "rank_cap": 8, "steps": 1, "warmup": 0, "ref_rank": 4,
+                        "precision": "fp64"})()
     assert bench.run_reference(ns) is None
