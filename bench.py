@@ -413,6 +413,45 @@ def run_reference(args):
     }
 
 
+def run_kernel_probe(args):
+    """A few launches of each local-matvec engine at the solve's working shapes (for ncu): the
+    binary32 contraction on CUDA cores and on the tcgen05 tensor cores, and the binary64 one,
+    through the C ABI on seeded Gaussian inputs.  Prints wall time per call (allocation and launch
+    overheads included; kernel durations come from the profiler)."""
+    import numpy as np
+    import torch
+    from paper_2501_12151_gb300 import tnfem
+    from paper_2501_12151_gb300 import workloads as W
+    r0, n, r1, a0, a1 = args.probe_shape
+    ctx = tnfem.Context(0)
+
+    def dev(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).cuda()
+
+    PhiL = W.rng(1).standard_normal((r0, a0, r0))
+    A = W.rng(2).standard_normal((a0, n, n, a1))
+    PhiR = W.rng(3).standard_normal((r1, a1, r1))
+    x = W.rng(4).standard_normal((r0, n, r1))
+    flops = 2.0 * n * r0 * r1 * (r0 * a0 + n * a0 * a1 + r1 * a1)
+    out = {"probe": "local matvec", "shape": {"r0": r0, "n": n, "r1": r1, "a0": a0, "a1": a1}, "flops": flops}
+    for dt, name in ((np.float32, "f32"), (np.float64, "f64")):
+        t = [dev(v, dt) for v in (PhiL, A, PhiR, x)]
+        y = torch.zeros(r0 * n * r1, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
+        for e in ((0, 1, 2) if dt == np.float32 else (None,)):
+            walls = []
+            for _ in range(args.probe_reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if e is None:
+                    ctx.op_local_matvec(r0, n, r1, a0, a1, *[v.data_ptr() for v in t], y.data_ptr())
+                else:
+                    ctx.op_local_matvec_f32(e, r0, n, r1, a0, a1, *[v.data_ptr() for v in t], y.data_ptr())
+                torch.cuda.synchronize()
+                walls.append(time.perf_counter() - t0)
+            out[f"{name}_engine{e if e is not None else 'fp64'}_wall_us"] = 1e6 * min(walls)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,8 +468,15 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--kernel-probe", action="store_true",
+                    help="only launch the local-matvec engines a few times at --probe-shape (for ncu)")
+    ap.add_argument("--probe-shape", type=int, nargs=5, default=[49, 4, 49, 51, 51], metavar=("R0", "N", "R1", "A0", "A1"))
+    ap.add_argument("--probe-reps", type=int, default=3)
     args = ap.parse_args(argv)
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.kernel_probe:
+        out = run_kernel_probe(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

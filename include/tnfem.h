@@ -288,7 +288,9 @@ tnfem_status tnfem_op_local_matvec_noalloc(void* stream, int r0, int n, int r1, 
                                            const double* x, double* y);
 /* Binary32 building blocks of the mixed-precision local solves (parity tests of both engines).
  * engine 0: CUDA-core FMA; engine 1: tcgen05 tensor cores, kind::tf32 with the three-term split
- * a b = a_hi b_hi + a_hi b_lo + a_lo b_hi (binary32-level accuracy from TF32 products).
+ * a b = a_hi b_hi + a_hi b_lo + a_lo b_hi (binary32-level accuracy from TF32 products), operands
+ * staged by ordinary loads; engine 2 (local matvec only): the same arithmetic on operands packed
+ * once into the tensor cores' tile layout and fed by bulk TMA copies, as the solver runs it.
  * tnfem_op_gemm_f32: C(b,m,n) = alpha sum_k A(b,m,k) B(b,k,n) + beta C(b,m,n) with element
  * (b,m,k) of A at A[b*sAb + m*sAm + k*sAk] (likewise B and C); every pointer is a device pointer to
  * binary32.  tnfem_op_local_matvec_f32: the contraction of tnfem_op_local_matvec in binary32. */

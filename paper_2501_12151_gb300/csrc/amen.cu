@@ -25,6 +25,8 @@
 #include "amen.h"
 #include "internal.h"
 #include "precond.h"
+#include "tc_gemm.h"
+#include "tc_matvec.h"
 
 namespace tnfem {
 
@@ -324,6 +326,11 @@ class Amen {
   int pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, U* y, const U* g,
               double gnorm, double rtol, const CgBufs<U>& b);
   int cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol);
+  // a bounded wait inside a tensor-core kernel ran out (recorded on the device)
+  void check_tc_error() {
+    if (ctx_->tensor_cores && tc_gemm_error(ctx_) != 0)
+      throw Error(TNFEM_E_TIMEOUT, "tensor-core kernel: bounded wait expired");
+  }
   void source_proj(int k, bool bra_z_left, bool bra_z_right, double* out, int ry0, int ry1);
   double* bra64(bool z, int k, int r0, int r1);
   void count_apply(int ry0, int ry1, int rx0, int rx1, int n, int a0, int a1) {
@@ -365,6 +372,20 @@ class Amen {
   long long local_refines_ = 0;
   long long breakdowns_ = 0;
   ChunkGraph graph_[2];  // conjugate-gradient chunk graphs, binary32 / binary64
+  TcMatvec tcmv_;        // binary32 local matvec on the tensor cores (packed operands)
+  bool tcmv_on_ = false; // tcmv_ holds the current local system
+  // local matvec of the current local system in precision U
+  template <typename U>
+  void matvec(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, const U* in, U* out,
+              U* ws, size_t wsn, const int* skip) {
+    if constexpr (std::is_same<U, float>::value) {
+      if (tcmv_on_) {
+        tcmv_.apply(ctx_, in, out, skip);
+        return;
+      }
+    }
+    local_matvec<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, in, out, ws, wsn, skip);
+  }
   double* host_ = nullptr;
   double flops_ = 0.0;
   long long iters_ = 0;
@@ -676,7 +697,7 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
   U* z = b.pre ? b.z : b.r;
   double** prz = b.pre ? prz_b : prr;
   TN_CHECK_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), ctx_->stream));
-  local_matvec<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, b.Bx, b.ws, b.wsn);
+  matvec<U>(r0, n, r1, a0, a1, PL, Ak, PR, y, b.Bx, b.ws, b.wsn, nullptr);
   count_apply(r0, r1, r0, r1, n, a0, a1);
   cg_init_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(g, b.Bx, b.r, b.p, N, prr[0]);
   count_launch(ctx_);
@@ -687,7 +708,7 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
     int cur = 0;
     for (int c = 0; c < kChunk; ++c) {
       const int nx = cur ^ 1;
-      local_matvec<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, b.p, b.Ap, b.ws, b.wsn, ctl);
+      matvec<U>(r0, n, r1, a0, a1, PL, Ak, PR, b.p, b.Ap, b.ws, b.wsn, ctl);
       {
         ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 2.0 * N * sizeof(U));
         cg_dot_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(b.p, b.Ap, N, ppap, ctl);
@@ -750,7 +771,23 @@ int Amen<T>::cg(int k, T* y, const T* g, double gnorm, double rtol) {
   const T* Ak = Acur(k);
   const bool pre = setup_pre<T>(r0, n, r1, a0, a1, PL, Ak, PR, bjw_);
   CgBufs<T> b{Bx_.p, r_.p, p_.p, Ap_.p, z_.p, wsT_.p, wsT_.n, pre};
-  return pcg_run<T>(r0, n, r1, a0, a1, PL, Ak, PR, y, g, gnorm, rtol, b);
+  if constexpr (std::is_same<T, float>::value) {
+    if (ctx_->tensor_cores) {
+      tcmv_.plan(ctx_, r0, n, r1, a0, a1);
+      tcmv_.prepare(ctx_, PL, Ak, PR);
+      tcmv_on_ = true;
+    }
+  }
+  int it = 0;
+  try {
+    it = pcg_run<T>(r0, n, r1, a0, a1, PL, Ak, PR, y, g, gnorm, rtol, b);
+  } catch (...) {
+    tcmv_on_ = false;
+    throw;
+  }
+  tcmv_on_ = false;
+  check_tc_error();
+  return it;
 }
 
 // Binary64 sweep, binary32 local solves: iterative refinement of the local system against its
@@ -774,6 +811,15 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
     const float* A32 = A_->p32[o_][k];
     const bool pre = setup_pre<float>(r0, n, r1, a0, a1, PL32_.p, A32, PR32_.p, bjw32_);
     CgBufs<float> b{Bx32_.p, r32_.p, p32_.p, Ap32_.p, z32_.p, ws32_.p, ws32_.n, pre};
+    if (ctx_->tensor_cores) {
+      tcmv_.plan(ctx_, r0, n, r1, a0, a1);
+      tcmv_.prepare(ctx_, PL32_.p, A32, PR32_.p);
+      tcmv_on_ = true;
+    }
+    struct Off {  // the tensor-core operands belong to this local system only
+      bool& f;
+      ~Off() { f = false; }
+    } off{tcmv_on_};
     int iters = 0;
     double prev = 0.0;
     for (int step = 0; step < 12; ++step) {
@@ -801,6 +847,7 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
       add_scaled_float_kernel<<<nblk((long long)N), RT, 0, ctx_->stream>>>(y, y32_.p, rn, N);
       count_launch(ctx_);
     }
+    check_tc_error();
     return iters;
   }
 }

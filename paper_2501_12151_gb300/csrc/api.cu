@@ -8,6 +8,8 @@
 #include "amen.h"
 #include "builder.h"
 #include "internal.h"
+#include "tc_gemm.h"
+#include "tc_matvec.h"
 
 using namespace tnfem;
 
@@ -726,11 +728,20 @@ tnfem_status tnfem_op_local_matvec_f32(tnfem_ctx* ctx, int engine, int r0, int n
   if (!ctx) return TNFEM_E_INVALID;
   return guard(ctx, [&] {
     TN_REQUIRE(PhiL && A && PhiR && x && y, "null pointer");
-    TN_REQUIRE(engine == 0 || engine == 1, "engine must be 0 (CUDA cores) or 1 (tensor cores)");
+    TN_REQUIRE(engine >= 0 && engine <= 2, "engine must be 0 (CUDA cores), 1 or 2 (tensor cores)");
     TN_REQUIRE(r0 >= 1 && r1 >= 1 && n >= 1 && a0 >= 1 && a1 >= 1, "sizes must be positive");
-    EngineScope es(ctx, engine);
+    EngineScope es(ctx, engine == 0 ? 0 : 1);
     DArr<float> Ap(ctx, (size_t)a0 * n * n * a1);
     transpose4_mid<float>(ctx, Ap.p, A, a0, n, n, a1);
+    if (engine == 2) {
+      TcMatvec mv;
+      mv.plan(ctx, r0, n, r1, a0, a1);
+      mv.prepare(ctx, PhiL, Ap.p, PhiR);
+      mv.apply(ctx, x, y, nullptr);
+      sync(ctx);
+      TN_REQUIRE(tc_gemm_error(ctx) == 0, "tensor-core kernel: bounded wait expired");
+      return;
+    }
     DArr<float> ws(ctx, local_ws_elems(r0, n, r1, a0, a1));
     local_matvec<float>(ctx, r0, n, r1, a0, a1, PhiL, Ap.p, PhiR, x, y, ws.p, ws.n);
     sync(ctx);

@@ -21,79 +21,17 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tc_common.cuh"
 #include "tc_gemm.h"
 
 namespace tnfem {
 
 namespace {
 
-constexpr int TM = 128;  // UMMA M
+using namespace tc;
 constexpr int KC = 32;   // K elements per staged chunk (4 MMA K steps of 8)
 constexpr int NT = 128;  // threads per CTA
 constexpr int kTileABytes = TM * KC * 4;  // one TF32 plane of the A tile
-constexpr long long kSpinLimit = 1ll << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-  uint32_t r;
-  asm volatile("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-
-// Shared-memory matrix descriptor, no swizzle, K-major: LBO = byte distance between core matrices
-// adjacent in K, SBO = between core matrices adjacent in M/N; bits 46..48 hold the fixed 0b001.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// Instruction descriptor of kind::tf32: D fp32, A and B TF32, both K-major, M = 128, N = tn.
-__host__ __device__ constexpr uint32_t make_idesc(int tn) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.b32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the given phase; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (long long i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(mbar, phase)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // offset in bytes of element (row, k) of a rows x KC tile in the core-matrix K-major layout
 __device__ __forceinline__ uint32_t tile_off(int row, int kg) {

@@ -1,6 +1,7 @@
-"""Binary32 contraction engines of the mixed-precision local solves: CUDA-core FMA (engine 0) and
-the tcgen05 tensor cores with the three-term TF32 split (engine 1), against the binary64
-definition on the same binary32 inputs.
+"""Binary32 contraction engines of the mixed-precision local solves: CUDA-core FMA (engine 0), the
+tcgen05 tensor cores with the three-term TF32 split on load-staged operands (engine 1) and on
+packed, TMA-fed operands (engine 2, the solver's local matvec), against the binary64 definition on
+the same binary32 inputs.
 
 Tolerance: both engines accumulate binary32 products; the split recovers binary32 accuracy from
 TF32 words (the dropped a_lo b_lo term is ~2^-22 of |a b|), so every element must agree with the
@@ -70,8 +71,9 @@ def test_gemm_f32(ctx, engine, M, N, K, batch, alay, shared):
     assert np.all(np.abs(got - ref) <= RTOL32 * scale + 1e-30)
 
 
-@pytest.mark.parametrize("engine", [0, 1])
-@pytest.mark.parametrize("r0,n,r1,a0,a1", [(5, 4, 7, 9, 11), (49, 4, 49, 51, 51), (33, 8, 20, 23, 17)])
+@pytest.mark.parametrize("engine", [0, 1, 2])
+@pytest.mark.parametrize("r0,n,r1,a0,a1", [(5, 4, 7, 9, 11), (49, 4, 49, 51, 51), (33, 8, 20, 23, 17),
+                                           (64, 4, 66, 51, 51), (1, 2, 4, 1, 43), (70, 8, 96, 30, 9)])
 def test_local_matvec_f32(ctx, engine, r0, n, r1, a0, a1):
     PhiL = _f32(W.rng(1).standard_normal((r0, a0, r0)))
     A = _f32(W.rng(2).standard_normal((a0, n, n, a1)))
