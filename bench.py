@@ -323,10 +323,12 @@ def run_ours(args):
         peak = FP64_NOMINAL_GFLOPS * 1e-3
         peak_note = "nominal GB300 binary64 rate (1.25 TFLOP/s)"
     share = {c: (prof[c]["ms"] * (prof[c]["launches"] / max(1, prof[c]["sampled"]))) for c in prof}
+    measured_fma = {"fp64": ctx.fma_peak("fp64"), "fp32": ctx.fma_peak("fp32")}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
                 "kernel": "gemm_kernel<float>" if cls == "contract32" else "gemm_kernel<double>",
                 "peak_source": peak_note,
+                "fma_peak_measured_tflops": measured_fma,
                 "launches": p["launches"], "sampled_launches": p["sampled"],
                 "avg_launch_us": (p["ms"] * 1e3 / p["sampled"]) if p["sampled"] else None,
                 "flops_per_launch": (p["flops"] / p["sampled"]) if p["sampled"] else None,

@@ -103,7 +103,10 @@ typedef struct {
   int local_maxit;     /* cap on conjugate-gradient iterations per local solve */
   int no_precond;      /* 0: block-Jacobi preconditioned local solves (default); 1: plain CG */
   int tensor_cores;    /* MIXED / MIXED_LOCAL: 1 runs the binary32 contractions on the tcgen05
-                          tensor cores (three-term TF32 split), 0 on CUDA-core FMA */
+                          tensor cores (TF32 split products), 0 on CUDA-core FMA */
+  double local_rtol;   /* each local solve stops at max(tol / 2, local_rtol * its starting relative
+                          residual); 0 solves every local system to tol / 2.  Default 1e-2 when the
+                          field is negative */
 } tnfem_solve_opts;
 
 typedef struct {
@@ -156,6 +159,10 @@ tnfem_status tnfem_profile_start(tnfem_ctx* ctx, int every);
  * algorithmic flops and bytes (any output pointer may be NULL). */
 tnfem_status tnfem_profile_read(tnfem_ctx* ctx, int cls, long long* launches, long long* sampled,
                                 double* ms, double* flops, double* bytes);
+/* Measured CUDA-core FMA rate of the context's device in TFLOP/s (precision 0: binary64,
+ * 1: binary32): register-resident FMA chains on 8 CTAs of 256 threads per SM, timed with events
+ * after one warm-up launch.  The denominator for the ALU-bound contraction kernels. */
+tnfem_status tnfem_measure_fma_peak(tnfem_ctx* ctx, int precision, double* tflops);
 
 /* ---- assembly (Algorithm 1, Section 5.2 / 5.3) ------------------------------------------- */
 

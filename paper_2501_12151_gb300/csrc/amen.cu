@@ -879,7 +879,10 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   // 3. local solve
   copy<T>(ctx_, y_.p, xk, N);
   if (res > prm_.tol / prm_.resid_damp && gnorm > 0) {
-    iters_ += cg(k, y_.p, g_.p, gnorm, prm_.tol / prm_.resid_damp);
+    // the local system is solved to a fraction of its own starting residual (not below tol / 2):
+    // the sweep's accuracy is set by the truncation, so tighter local solves only cost iterations
+    const double rtol = std::max(prm_.tol / prm_.resid_damp, prm_.local_rtol * res);
+    iters_ += cg(k, y_.p, g_.p, gnorm, rtol);
     diff_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(r_.p, y_.p, xk, N, part_.p);
     sum_partials_kernel<<<1, RT, 0, ctx_->stream>>>(part_.p, c64_.p);
     count_launch(ctx_, 2);

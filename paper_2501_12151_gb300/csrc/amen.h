@@ -21,7 +21,8 @@ struct AmenParams {
   int kick = 4;             // enrichment rank
   int max_sweeps = 40;
   int local_maxit = 500;    // conjugate-gradient iterations per local solve
-  double resid_damp = 2.0;  // local solves stop at tol / resid_damp
+  double resid_damp = 2.0;  // local solves stop at tol / resid_damp ...
+  double local_rtol = 1e-2; // ... or at local_rtol times their starting residual, whichever is larger
   bool precond = true;      // block-Jacobi preconditioned conjugate gradients for the local solves
   bool local_mixed = false; // binary64 sweep with binary32 local solves refined in binary64
   bool graphs = true;       // replay the conjugate-gradient chunks as CUDA graphs

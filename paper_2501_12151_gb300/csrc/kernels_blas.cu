@@ -15,10 +15,12 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, GT = 256;
 
+// With `flat`, B is shared by all batches and the rows of a tile are the flattened (batch, m)
+// pairs (row R = b * M + m), so small per-batch M does not leave tiles idle.
 template <typename T>
 __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* __restrict__ A,
                                                   const T* __restrict__ B, T beta, T* __restrict__ C,
-                                                  T* __restrict__ work, int splits, int kchunk,
+                                                  T* __restrict__ work, int splits, int kchunk, int flat,
                                                   const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ T As[BK][BM + 1];
@@ -27,13 +29,26 @@ __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* 
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int bz = blockIdx.z;
-  const int b = bz / splits, sp = bz % splits;
+  const int b = flat ? 0 : bz / splits, sp = bz % splits;
   const int kbeg = sp * kchunk;
   const int kend = min(g.K, kbeg + kchunk);
+  const long long rows = flat ? (long long)g.M * g.batch : g.M;
   const T* Ab = A + (long long)b * g.sAb;
   const T* Bb = B + (long long)b * g.sBb;
   const bool a_k_fast = (g.sAk == 1);
   const bool b_n_fast = (g.sBn == 1);
+  // row offsets of this thread's four A loads (fixed over the K loop)
+  long long a_off[4];
+  bool a_ok[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int idx = tid + i * GT;
+    const int mm = a_k_fast ? idx / BK : idx % BM;
+    const long long R = m0 + mm;
+    a_ok[i] = R < rows;
+    const long long bb = flat ? R / g.M : 0, m = flat ? R - bb * g.M : R;
+    a_off[i] = bb * g.sAb + m * g.sAm;
+  }
   T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -45,9 +60,9 @@ __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* 
       int idx = tid + i * GT;
       int mm, kk;
       if (a_k_fast) { kk = idx % BK; mm = idx / BK; } else { mm = idx % BM; kk = idx / BM; }
-      int gm = m0 + mm, gk = k0 + kk;
+      int gk = k0 + kk;
       T v = T(0);
-      if (gm < g.M && gk < kend) v = Ab[(long long)gm * g.sAm + (long long)gk * g.sAk];
+      if (a_ok[i] && gk < kend) v = Ab[a_off[i] + (long long)gk * g.sAk];
       As[kk][mm] = v;
     }
 #pragma unroll
@@ -79,29 +94,32 @@ __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* 
     T* Cb = C + (long long)b * g.sCb;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      int gm = m0 + ty + 16 * i;
-      if (gm >= g.M) continue;
+      const long long R = m0 + ty + 16 * i;
+      if (R >= rows) continue;
+      const long long bb = flat ? R / g.M : 0, m = flat ? R - bb * g.M : R;
+      T* crow = Cb + bb * g.sCb + m * g.sCm;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         int gn = n0 + tx + 16 * j;
         if (gn >= g.N) continue;
-        T* c = Cb + (long long)gm * g.sCm + (long long)gn * g.sCn;
+        T* c = crow + (long long)gn * g.sCn;
         T v = alpha * acc[i][j];
         if (beta != T(0)) v += beta * (*c);
         *c = v;
       }
     }
   } else {
+    // partials [split][batch][M][N]; flattened rows index (batch, m) in the same order
     T* W = work + ((long long)sp * g.batch + b) * (long long)g.M * g.N;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      int gm = m0 + ty + 16 * i;
-      if (gm >= g.M) continue;
+      const long long R = m0 + ty + 16 * i;
+      if (R >= rows) continue;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         int gn = n0 + tx + 16 * j;
         if (gn >= g.N) continue;
-        W[(long long)gm * g.N + gn] = acc[i][j];
+        W[R * g.N + gn] = acc[i][j];
       }
     }
   }
@@ -281,11 +299,15 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
       return;
     }
   }
-  int tiles_m = (g.M + BM - 1) / BM, tiles_n = (g.N + BN - 1) / BN;
-  long long tiles = (long long)tiles_m * tiles_n * g.batch;
+  const int flat = (g.sBb == 0 && g.batch > 1) ? 1 : 0;
+  const long long rows = flat ? (long long)g.M * g.batch : g.M;
+  int tiles_m = (int)((rows + BM - 1) / BM), tiles_n = (g.N + BN - 1) / BN;
+  long long tiles = (long long)tiles_m * tiles_n * (flat ? 1 : g.batch);
   int splits = 1;
-  const long long target = 2 * 152;
-  if (work && tiles < target && g.K >= 4 * BK) {
+  // split K only when the tiles alone fill well under one wave and K is long: the partial sums
+  // cost a second kernel
+  const long long target = 152;
+  if (work && tiles < target / 2 && g.K >= 8 * BK) {
     long long want = (target + tiles - 1) / tiles;
     long long maxs = g.K / (2 * BK);
     long long fit = (long long)(work_elems / ((size_t)g.batch * g.M * g.N));
@@ -294,14 +316,14 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
   int kchunk = (g.K + splits - 1) / splits;
   kchunk = ((kchunk + BK - 1) / BK) * BK;
   splits = (g.K + kchunk - 1) / kchunk;
-  dim3 grid(tiles_n, tiles_m, g.batch * splits);
-  TN_REQUIRE(g.batch * (long long)splits < 65536, "gemm: batch too large");
+  dim3 grid(tiles_n, tiles_m, (flat ? 1 : g.batch) * splits);
+  TN_REQUIRE((flat ? 1 : g.batch) * (long long)splits < 65536 && tiles_m < 65536, "gemm: grid too large");
   {
     const double mnk = (double)g.M * g.N * g.K * g.batch;
     const double words = ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N) * g.batch;
     ProfScope ps(ctx, sizeof(T) == 8 ? TNFEM_PROF_CONTRACT64 : TNFEM_PROF_CONTRACT32, 2.0 * mnk,
                  words * sizeof(T));
-    gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, skip);
+    gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip);
   }
   count_launch(ctx);
   if (splits > 1) {

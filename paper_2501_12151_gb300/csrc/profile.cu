@@ -117,3 +117,64 @@ tnfem_status tnfem_profile_read(tnfem_ctx* ctx, int cls, long long* launches, lo
 }
 
 }  // extern "C"
+
+// ---- arithmetic peaks --------------------------------------------------------------------------
+// Register-resident FMA chains (8 independent chains per thread, no memory traffic) over a grid of
+// 8 CTAs of 256 threads per SM: the CUDA-core FMA rate the contraction kernels can approach.
+namespace tnfem {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(T* out, int iters, T seed) {
+  T a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = seed + (T)(threadIdx.x + c);
+  const T b = (T)0.999999, d = (T)1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], b, d);
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += a[c];
+  if (s == (T)-1) out[0] = s;  // never true; keeps the chains live
+}
+
+}  // namespace
+}  // namespace tnfem
+
+extern "C" tnfem_status tnfem_measure_fma_peak(tnfem_ctx* ctx, int precision, double* tflops) {
+  if (!ctx || !tflops || (precision != 0 && precision != 1)) return TNFEM_E_INVALID;
+  try {
+    int sms = 0;
+    TN_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int blocks = sms * 8, threads = 256;
+    const int iters = precision == 0 ? 2048 : 65536;
+    cudaEvent_t e0, e1;
+    TN_CHECK_CUDA(cudaEventCreate(&e0));
+    TN_CHECK_CUDA(cudaEventCreate(&e1));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up clocks and code
+      TN_CHECK_CUDA(cudaEventRecord(e0, ctx->stream));
+      if (precision == 0)
+        fma_peak_kernel<double><<<blocks, threads, 0, ctx->stream>>>(reinterpret_cast<double*>(ctx->scratch), iters,
+                                                                      1.0);
+      else
+        fma_peak_kernel<float><<<blocks, threads, 0, ctx->stream>>>(reinterpret_cast<float*>(ctx->scratch), iters,
+                                                                     1.0f);
+      count_launch(ctx);
+      TN_CHECK_CUDA(cudaEventRecord(e1, ctx->stream));
+      TN_CHECK_CUDA(cudaEventSynchronize(e1));
+      TN_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    *tflops = ms > 0 ? flops / (ms * 1e-3) * 1e-12 : 0.0;
+  } catch (const Error& e) {
+    ctx->err = e.what();
+    cudaGetLastError();
+    return e.status;
+  }
+  return TNFEM_OK;
+}

@@ -6,19 +6,21 @@
 //   stage 3  y[(a',i)][b']        = T2[(a',i)][(g,b)] . PhiR[b'][(g,b)]       K = a1 r1
 //
 // Every operand lives in HBM in the "packed" layout the MMAs read: tiles of RB rows x 32 K of TF32
-// words, a hi plane (tf32(v)) followed by a lo plane (tf32(v - hi)), each plane in the canonical
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix).  A whole tile is one
+// words, three planes hi = tf32(v), mid = tf32(v - hi), lo = tf32(v - hi - mid) (33 significant
+// bits, more than binary32's 24), each plane in the canonical no-swizzle K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix).  A whole tile is one
 // contiguous block, so a CTA stages it with a single cp.async.bulk into shared memory and the
 // tensor cores read it from there unchanged.  The constant operands (PhiL, the operator core,
 // PhiR) are packed once per local solve; x is packed once per matvec; stages 1 and 2 write their
 // products straight into the packed layout of the next stage's A operand (the stage maps below),
-// so no intermediate is ever re-read in plain form.  The three-term split (hi.hi + hi.lo + lo.hi,
-// three MMAs per K step) keeps binary32 accuracy.
+// so no intermediate is ever re-read in plain form.  Six MMAs per K step (hi.hi, hi.mid, mid.hi,
+// hi.lo, mid.mid, lo.hi: every product down to 2^-33 relative) leave binary32 accumulation in
+// tensor memory as the only rounding, i.e. the accuracy of a binary32 CUDA-core contraction.
 //
-// Stage 3 has a long K (a1 r1); its K range is split over CTAs whose partial tiles are summed, in a
-// fixed order, by the last CTA of each output tile to arrive (an atomic counter; no CTA waits on
-// another).  Every mbarrier wait is bounded; on expiry the CTA records an error, skips its output,
-// frees its tensor memory and returns.
+// Stage 3 has a long K (a1 r1); its K range is split over CTAs whose partial products are summed in
+// split order by a small reduction kernel (deterministic, no atomics).  Every mbarrier wait is
+// bounded; on expiry the CTA records an error, skips its output, frees its tensor memory and
+// returns.
 #include <algorithm>
 
 #include "internal.h"
@@ -35,21 +37,29 @@ constexpr int KCH = 32;        // K words per tile
 constexpr int TN = 64;         // N of every MMA here
 constexpr int STAGES = 3;      // TMA pipeline depth
 constexpr int NT = 128;        // threads per CTA
+constexpr int NP = 3;          // TF32 planes per operand: hi, mid, lo
 constexpr int kPlaneA = TM * KCH * 4;      // bytes of one TF32 plane of an A tile
 constexpr int kPlaneB = TN * KCH * 4;      // ... of a B tile
-constexpr int kTileA = 2 * kPlaneA;        // hi + lo
-constexpr int kTileB = 2 * kPlaneB;
+constexpr int kTileA = NP * kPlaneA;
+constexpr int kTileB = NP * kPlaneB;
 constexpr int kStageBytes = kTileA + kTileB;
 
 __device__ __forceinline__ uint32_t core_off(int row, int kg) {
   return (uint32_t)((row >> 3) * (KCH / 4) * 128 + kg * 128 + (row & 7) * 16);
 }
 
-// word offset of element (row, k) in plane `plane` of a packed operand with tiles of rb rows
-__device__ __forceinline__ long long packed_word(int row, int k, int rb, int nkc, int plane) {
-  const long long tile = (long long)(row / rb) * nkc + k / KCH;
-  const int r = row % rb, kk = k % KCH;
-  return tile * (2ll * rb * KCH) + (long long)plane * rb * KCH + core_off(r, kk >> 2) / 4 + (kk & 3);
+// word offset of element (row, k) in plane 0 of a packed operand with tiles of TM rows
+__device__ __forceinline__ long long packed_word_tm(int row, int k, int nkc) {
+  const long long tile = (long long)(row >> 7) * nkc + (k >> 5);
+  const int r = row & (TM - 1), kk = k & (KCH - 1);
+  return tile * ((long long)NP * TM * KCH) + core_off(r, kk >> 2) / 4 + (kk & 3);
+}
+
+__device__ __forceinline__ void split3(float v, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+  hi = to_tf32(v);
+  const float r1 = v - __uint_as_float(hi);
+  mid = to_tf32(r1);
+  lo = to_tf32(r1 - __uint_as_float(mid));
 }
 
 // dst = packed(src): element (row, k) = src[row * sr + k * sk] for row < rows, k < K, zero beyond.
@@ -60,18 +70,18 @@ __global__ void pack_kernel(uint32_t* __restrict__ dst, const float* __restrict_
        t += (long long)gridDim.x * blockDim.x) {
     const int row = (int)(t / (nkc * (KCH / 4)));
     const int kg = (int)(t % (nkc * (KCH / 4)));
-    uint32_t hi[4], lo[4];
+    uint32_t hi[4], mid[4], lo[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k = kg * 4 + e;
       const float v = (row < rows && k < K) ? src[row * sr + k * sk] : 0.f;
-      hi[e] = to_tf32(v);
-      lo[e] = to_tf32(v - __uint_as_float(hi[e]));
+      split3(v, hi[e], mid[e], lo[e]);
     }
     const long long tile = (long long)(row / rb) * nkc + (kg * 4) / KCH;
-    const long long base = tile * (2ll * rb * KCH) + core_off(row % rb, kg % (KCH / 4)) / 4;
+    const long long base = tile * ((long long)NP * rb * KCH) + core_off(row % rb, kg % (KCH / 4)) / 4;
     *reinterpret_cast<uint4*>(dst + base) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(dst + base + rb * KCH) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(dst + base + rb * KCH) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
+    *reinterpret_cast<uint4*>(dst + base + 2 * rb * KCH) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
@@ -87,10 +97,9 @@ struct StageArgs {
   uint32_t* D;
   int d_nkc;
   int dm, dn, mr, mk;
-  // EPI_PLAIN: y[m * N + n]; split-K partials and per-tile counters
+  // EPI_PLAIN: y[m * N + n], or split-K partials work[split][m][n] when splits > 1
   float* Y;
   float* work;
-  int* counters;
   int* err;
   const int* skip;
 };
@@ -102,7 +111,6 @@ __global__ void __launch_bounds__(NT) tc_stage_kernel(StageArgs g) {
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rbA = blockIdx.x, rbB = blockIdx.y, sp = blockIdx.z;
   const int c0 = sp * g.kc_per_split;
@@ -143,16 +151,22 @@ __global__ void __launch_bounds__(NT) tc_stage_kernel(StageArgs g) {
       if (!mbar_wait(smem_u32(&full[s]), fph[s])) { ok = false; break; }
       fph[s] ^= 1u;
       fence_after();
-      const uint32_t a_hi = sbase + s * kStageBytes, a_lo = a_hi + kPlaneA;
-      const uint32_t b_hi = a_hi + kTileA, b_lo = b_hi + kPlaneB;
+      const uint32_t a0p = sbase + s * kStageBytes;
+      const uint32_t b0p = a0p + kTileA;
 #pragma unroll
       for (int st = 0; st < KCH / 8; ++st) {
         const uint32_t ko = st * 256;
-        const uint64_t dah = make_desc(a_hi + ko, lbo, sbo), dal = make_desc(a_lo + ko, lbo, sbo);
-        const uint64_t dbh = make_desc(b_hi + ko, lbo, sbo), dbl = make_desc(b_lo + ko, lbo, sbo);
-        mma_tf32(tmem, dah, dbh, idesc, (i > 0 || st > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
+        const uint64_t da0 = make_desc(a0p + ko, lbo, sbo), da1 = make_desc(a0p + kPlaneA + ko, lbo, sbo),
+                       da2 = make_desc(a0p + 2 * kPlaneA + ko, lbo, sbo);
+        const uint64_t db0 = make_desc(b0p + ko, lbo, sbo), db1 = make_desc(b0p + kPlaneB + ko, lbo, sbo),
+                       db2 = make_desc(b0p + 2 * kPlaneB + ko, lbo, sbo);
+        // small terms first: hi.lo, mid.mid, lo.hi, hi.mid, mid.hi, hi.hi
+        mma_tf32(tmem, da0, db2, idesc, (i > 0 || st > 0) ? 1u : 0u);
+        mma_tf32(tmem, da1, db1, idesc, 1u);
+        mma_tf32(tmem, da2, db0, idesc, 1u);
+        mma_tf32(tmem, da0, db1, idesc, 1u);
+        mma_tf32(tmem, da1, db0, idesc, 1u);
+        mma_tf32(tmem, da0, db0, idesc, 1u);
       }
       mma_commit(smem_u32(&empty[s]));
       // refill the stage of the previous chunk once its MMAs (issued one step ago) are done
@@ -173,58 +187,39 @@ __global__ void __launch_bounds__(NT) tc_stage_kernel(StageArgs g) {
     const int r = warp * 32 + lane;       // TMEM lane = row of the tile
     const int m = rbA * TM + r;
     const bool row_ok = m < g.rows;
-    float* part = nullptr;
-    if (EPI == EPI_PLAIN && g.splits > 1)
-      part = g.work + (((long long)(rbA * gridDim.y + rbB) * g.splits + sp) * TM + r) * TN;
+    // per-row part of the stage map (one division per row, none per element)
+    const int qa = row_ok && EPI != EPI_PLAIN ? m / g.dm : 0;
+    const int ra = row_ok && EPI != EPI_PLAIN ? m - qa * g.dm : 0;
+    float* part = (EPI == EPI_PLAIN && g.splits > 1) ? g.work + (long long)sp * g.rows * g.N : nullptr;
 #pragma unroll 1
     for (int cc = 0; cc < TN; cc += 16) {
       uint32_t v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
       if (!row_ok) continue;
+      const int nb = rbB * TN + cc;
+      if (EPI == EPI_PLAIN) {
+        float* dst = part ? part + (long long)m * g.N : g.Y + (long long)m * g.N;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int n = rbB * TN + cc + e;
-        const float val = __uint_as_float(v[e]);
-        if (EPI == EPI_PLAIN) {
-          if (part) part[cc + e] = val;
-          else if (n < g.N) g.Y[(long long)m * g.N + n] = val;
-        } else if (n < g.N) {
-          int row2, k2;
-          if (EPI == EPI_STAGE1) {  // m = a' dm + beta, n = j dn + b  ->  (a' mr + b, beta mk + j)
-            row2 = (m / g.dm) * g.mr + (n % g.dn);
-            k2 = (m % g.dm) * g.mk + (n / g.dn);
-          } else {                  // m = a' dm + b, n = i dn + g  ->  (a' mr + i, g mk + b)
-            row2 = (m / g.dm) * g.mr + (n / g.dn);
-            k2 = (n % g.dn) * g.mk + (m % g.dm);
+        for (int e = 0; e < 16; ++e)
+          if (nb + e < g.N) dst[nb + e] = __uint_as_float(v[e]);
+      } else {
+        int q = nb / g.dn, rr = nb - q * g.dn;  // n = q dn + rr, advanced incrementally
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          if (nb + e < g.N) {
+            // stage 1: m = a' dm + beta, n = j dn + b  ->  (a' mr + b, beta mk + j)
+            // stage 2: m = a' dm + b,    n = i dn + g  ->  (a' mr + i, g mk + b)
+            const int row2 = EPI == EPI_STAGE1 ? qa * g.mr + rr : qa * g.mr + q;
+            const int k2 = EPI == EPI_STAGE1 ? ra * g.mk + q : rr * g.mk + ra;
+            uint32_t hi, mid, lo;
+            split3(__uint_as_float(v[e]), hi, mid, lo);
+            const long long w = packed_word_tm(row2, k2, g.d_nkc);
+            g.D[w] = hi;
+            g.D[w + TM * KCH] = mid;
+            g.D[w + 2 * TM * KCH] = lo;
           }
-          const uint32_t hi = to_tf32(val);
-          const uint32_t lo = to_tf32(val - __uint_as_float(hi));
-          g.D[packed_word(row2, k2, TM, g.d_nkc, 0)] = hi;
-          g.D[packed_word(row2, k2, TM, g.d_nkc, 1)] = lo;
+          if (++rr == g.dn) { rr = 0; ++q; }
         }
-      }
-    }
-    if (EPI == EPI_PLAIN && g.splits > 1) {
-      // the last CTA of this output tile to finish sums the partials in split order
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) {
-        const int prev = atomicAdd(&g.counters[rbA * gridDim.y + rbB], 1);
-        s_last = (prev == g.splits - 1) ? 1 : 0;
-      }
-      __syncthreads();
-      if (s_last) {
-        __threadfence();
-        const float* base = g.work + ((long long)(rbA * gridDim.y + rbB) * g.splits) * TM * TN;
-        for (int t = tid; t < TM * TN; t += NT) {
-          const int rr = t / TN, cn = t % TN;
-          const int mm = rbA * TM + rr, nn = rbB * TN + cn;
-          if (mm >= g.rows || nn >= g.N) continue;
-          float acc = 0.f;
-          for (int q = 0; q < g.splits; ++q) acc += base[(long long)q * TM * TN + t];
-          g.Y[(long long)mm * g.N + nn] = acc;
-        }
-        if (tid == 0) g.counters[rbA * gridDim.y + rbB] = 0;
       }
     }
   } else if (tid == 0) {
@@ -264,7 +259,7 @@ void TcMatvec::plan(tnfem_ctx* ctx, int r0_, int n_, int r1_, int a0_, int a1_) 
   ap = dims(n * a1, a0 * n, TN);     // stage 2 B: rows (i,g), K = (beta,j)
   t2 = dims(r0 * n, a1 * r1, TM);    // stage 3 A: rows (a',i), K = (g,b)
   pr = dims(r1, a1 * r1, TN);        // stage 3 B: rows b', K = (g,b)
-  auto words = [](const PackDims& d) { return (size_t)d.nrb * d.nkc * 2 * d.rb * KCH; };
+  auto words = [](const PackDims& d) { return (size_t)d.nrb * d.nkc * NP * d.rb * KCH; };
   PL.ensure(ctx, words(pl));
   XP.ensure(ctx, words(xp));
   T1.ensure(ctx, words(t1));
@@ -276,11 +271,7 @@ void TcMatvec::plan(tnfem_ctx* ctx, int r0_, int n_, int r1_, int a0_, int a1_) 
   splits3 = std::max(1, std::min(cdiv(t2.nkc, 4), std::max(1, 152 / tiles3)));
   kc3 = cdiv(t2.nkc, splits3);
   splits3 = cdiv(t2.nkc, kc3);
-  work.ensure(ctx, (size_t)tiles3 * splits3 * TM * TN);
-  if (counters.n < (size_t)tiles3) {
-    counters.ensure(ctx, (size_t)tiles3);
-    TN_CHECK_CUDA(cudaMemsetAsync(counters.p, 0, counters.n * sizeof(int), ctx->stream));
-  }
+  work.ensure(ctx, (size_t)splits3 * r0 * n * r1);
   // padding of the packed intermediates must read as zero; the products rewrite the rest
   TN_CHECK_CUDA(cudaMemsetAsync(T1.p, 0, words(t1) * sizeof(uint32_t), ctx->stream));
   TN_CHECK_CUDA(cudaMemsetAsync(T2.p, 0, words(t2) * sizeof(uint32_t), ctx->stream));
@@ -324,9 +315,13 @@ void TcMatvec::apply(tnfem_ctx* ctx, const float* x, float* y, const int* skip) 
   StageArgs s3{};
   s3.A = T2.p; s3.B = PR.p; s3.nkc = t2.nkc; s3.rows = r0 * n; s3.N = r1;
   s3.splits = splits3; s3.kc_per_split = kc3;
-  s3.Y = y; s3.work = work.p; s3.counters = counters.p;
+  s3.Y = y; s3.work = work.p;
   s3.err = err; s3.skip = skip;
   launch_stage<EPI_PLAIN>(ctx, s3, t2.nrb, pr.nrb, splits3, f3, 4.0 * (r0 * n * a1 * r1 + r1 * a1 * r1 + r0 * n * r1));
+  if (splits3 > 1) {
+    GemmDesc gr{r0 * n, r1, 1, 1, 0, 0, 0, 0, 0, 0, r1, 1, 0};
+    splitk_reduce<float>(ctx, gr, 1.0f, 0.0f, y, work.p, splits3, skip);
+  }
   check_launch(ctx, "tensor-core matvec");
 }
 

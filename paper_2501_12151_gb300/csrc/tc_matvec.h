@@ -8,7 +8,7 @@
 
 namespace tnfem {
 
-// A matrix of `rows` x `K` packed into tiles of `rb` rows x 32 K (TF32 hi and lo planes).
+// A matrix of `rows` x `K` packed into tiles of `rb` rows x 32 K (TF32 hi, mid and lo planes).
 struct PackDims {
   int rows = 0, K = 0, rb = 0, nrb = 0, nkc = 0;
 };
@@ -17,8 +17,7 @@ struct TcMatvec {
   int r0 = 0, n = 0, r1 = 0, a0 = 0, a1 = 0;
   PackDims pl, xp, t1, ap, t2, pr;
   DArr<uint32_t> PL, XP, T1, AP, T2, PR;  // packed operands and intermediates
-  DArr<float> work;                       // split-K partial tiles of stage 3
-  DArr<int> counters;                     // per output tile of stage 3 (reset by the last CTA)
+  DArr<float> work;                       // split-K partial products of stage 3 [split][m][n]
   int splits3 = 1, kc3 = 1;
   // size the buffers for one local system (zeroes the padding of the intermediates)
   void plan(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1);

@@ -49,7 +49,7 @@ class COpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("rank_cap", C.c_int), ("kickrank", C.c_int), ("max_sweeps", C.c_int),
                 ("precision", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int),
                 ("seed", C.c_uint64), ("local_maxit", C.c_int), ("no_precond", C.c_int),
-                ("tensor_cores", C.c_int)]
+                ("tensor_cores", C.c_int), ("local_rtol", C.c_double)]
 
 
 class CInfo(C.Structure):
@@ -114,6 +114,7 @@ _sig("tnfem_op_local_matvec_noalloc", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _v
 _ll = C.c_longlong
 _sig("tnfem_op_gemm_f32", _i, [_vp, _i, _i, _i, _i, _i] + [_ll] * 9 + [C.c_float, _vp, _vp, C.c_float, _vp])
 _sig("tnfem_op_local_matvec_f32", _i, [_vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
+_sig("tnfem_measure_fma_peak", _i, [_vp, _i, _pd])
 _sig("tnfem_profile_start", _i, [_vp, _i])
 _sig("tnfem_profile_read", _i, [_vp, _i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pd, _pd, _pd])
 
@@ -185,6 +186,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.local_maxit = int(local_maxit)
     co.no_precond = 0 if getattr(o, "precond", True) else 1
     co.tensor_cores = 1 if getattr(o, "tensor_cores", False) else 0
+    co.local_rtol = float(getattr(o, "local_rtol", -1.0))
     return co
 
 
@@ -294,6 +296,12 @@ class Context:
 
     def set_stream(self, stream: int):
         self.check(lib.tnfem_set_stream(self.h, C.c_void_p(stream)))
+
+    def fma_peak(self, precision: str) -> float:
+        """Measured CUDA-core FMA rate in TFLOP/s ("fp64" or "fp32")."""
+        v = C.c_double()
+        self.check(lib.tnfem_measure_fma_peak(self.h, 0 if precision == "fp64" else 1, C.byref(v)))
+        return v.value
 
     def profile_start(self, every: int = 1):
         """Time every ``every``-th launch of each kernel class with CUDA events (0 stops)."""
