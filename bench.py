@@ -322,7 +322,11 @@ def run_ours(args):
     else:
         peak = FP64_NOMINAL_GFLOPS * 1e-3
         peak_note = "nominal GB300 binary64 rate (1.25 TFLOP/s)"
-    share = {c: (prof[c]["ms"] * (prof[c]["launches"] / max(1, prof[c]["sampled"]))) for c in prof}
+    # per class: launches seen in the timed region, how many were timed (events outside graphs,
+    # device timers inside them) and the mean device time of a timed launch
+    by_class = {c: {"launches": prof[c]["launches"], "timed": prof[c]["sampled"],
+                    "mean_us": (prof[c]["ms"] * 1e3 / prof[c]["sampled"]) if prof[c]["sampled"] else None}
+                for c in prof}
     measured_fma = {"fp64": ctx.fma_peak("fp64"), "fp32": ctx.fma_peak("fp32")}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
@@ -332,7 +336,8 @@ def run_ours(args):
                 "launches": p["launches"], "sampled_launches": p["sampled"],
                 "avg_launch_us": (p["ms"] * 1e3 / p["sampled"]) if p["sampled"] else None,
                 "flops_per_launch": (p["flops"] / p["sampled"]) if p["sampled"] else None,
-                "est_device_ms_by_class": share}
+                "timing": "device globaltimer per launch inside CUDA graphs, CUDA events outside",
+                "by_class": by_class}
 
     cpu = None
     if not args.no_cpu_baseline:

@@ -67,6 +67,15 @@ struct tnfem_ctx {
   double prof_bytes[TNFEM_PROF_CLASSES] = {};
   std::vector<ProfEv> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
+  // device-side timers of sampled launches captured into graphs (see tnfem::KTimer)
+  struct ProfTimer {
+    int slot;
+    int cls;
+    double flops, bytes;
+  };
+  struct KTimerPool;
+  KTimerPool* ktimers = nullptr;
+  std::vector<ProfTimer> prof_timers;
 };
 
 namespace tnfem {
@@ -87,6 +96,45 @@ struct ProfScope {
   ProfScope(tnfem_ctx* c, int cls, double flops, double bytes);
   ~ProfScope();
 };
+
+// Device-side duration of one kernel launch, accumulated over every execution of that launch
+// (including each replay of a graph that captured it): the first CTA to start records the
+// global timer, every CTA records its end, and the last CTA to finish adds end - start to
+// `total_ns` and increments `count`.  Used for launches inside CUDA graphs, where events cannot
+// bracket single kernels.
+struct KTimer {
+  unsigned long long start, end, total_ns;
+  unsigned int arrived, count;
+};
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void ktimer_begin(KTimer* t) {
+  if (t && threadIdx.x == 0) atomicMin(&t->start, global_ns());
+}
+// Call once per CTA after its last store (all threads of the CTA reach it).
+__device__ __forceinline__ void ktimer_end(KTimer* t) {
+  if (!t) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&t->end, global_ns());
+    __threadfence();
+    const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
+    if (atomicAdd(&t->arrived, 1u) == nblk - 1) {
+      __threadfence();
+      const unsigned long long s = atomicAdd(&t->start, 0ull), e = atomicAdd(&t->end, 0ull);
+      t->total_ns += e - s;
+      t->count += 1;
+      t->start = ~0ull;
+      t->end = 0ull;
+      t->arrived = 0u;
+    }
+  }
+}
+// A sampled launch that is being captured into a graph gets a timer slot (nullptr otherwise).
+KTimer* prof_ktimer(tnfem_ctx* ctx, int cls, double flops, double bytes);
 void prof_resolve(tnfem_ctx* ctx);
 void prof_release(tnfem_ctx* ctx);
 void check_launch(tnfem_ctx* ctx, const char* what);

@@ -21,8 +21,9 @@ template <typename T>
 __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* __restrict__ A,
                                                   const T* __restrict__ B, T beta, T* __restrict__ C,
                                                   T* __restrict__ work, int splits, int kchunk, int flat,
-                                                  const int* __restrict__ skip) {
+                                                  const int* __restrict__ skip, KTimer* __restrict__ timer) {
   if (skip && *skip) return;
+  ktimer_begin(timer);
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* 
       }
     }
   }
+  ktimer_end(timer);
 }
 
 template <typename T>
@@ -321,9 +323,10 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
   {
     const double mnk = (double)g.M * g.N * g.K * g.batch;
     const double words = ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N) * g.batch;
-    ProfScope ps(ctx, sizeof(T) == 8 ? TNFEM_PROF_CONTRACT64 : TNFEM_PROF_CONTRACT32, 2.0 * mnk,
-                 words * sizeof(T));
-    gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip);
+    const int cls = sizeof(T) == 8 ? TNFEM_PROF_CONTRACT64 : TNFEM_PROF_CONTRACT32;
+    KTimer* timer = prof_ktimer(ctx, cls, 2.0 * mnk, words * sizeof(T));
+    ProfScope ps(ctx, cls, 2.0 * mnk, words * sizeof(T));
+    gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip, timer);
   }
   count_launch(ctx);
   if (splits > 1) {

@@ -22,9 +22,57 @@ cudaEvent_t take_event(tnfem_ctx* ctx) {
 
 }  // namespace
 
+}  // namespace tnfem
+
+struct tnfem_ctx::KTimerPool {
+  tnfem::KTimer* dev = nullptr;
+  int cap = 0, used = 0;
+};
+
+namespace tnfem {
+
+namespace {
+__global__ void ktimer_init_kernel(KTimer* t, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    t[i] = KTimer{~0ull, 0ull, 0ull, 0u, 0u};
+}
+constexpr int kTimerSlots = 4096;
+}  // namespace
+
+// Allocate (once) and reset the timer slots; only outside stream capture.
+void ktimers_reset(tnfem_ctx* ctx) {
+  if (!ctx->ktimers) {
+    auto* p = new tnfem_ctx::KTimerPool();
+    try {
+      p->dev = static_cast<KTimer*>(dalloc(ctx, kTimerSlots * sizeof(KTimer)));
+    } catch (...) {
+      delete p;
+      throw;
+    }
+    p->cap = kTimerSlots;
+    ctx->ktimers = p;
+  }
+  ktimer_init_kernel<<<(kTimerSlots + 255) / 256, 256, 0, ctx->stream>>>(ctx->ktimers->dev, kTimerSlots);
+  ctx->ktimers->used = 0;
+  ctx->prof_timers.clear();
+}
+
+KTimer* prof_ktimer(tnfem_ctx* ctx, int cls, double flops, double bytes) {
+  if (ctx->prof_every <= 0 || !ctx->capturing || !ctx->ktimers || cls < 0 || cls >= TNFEM_PROF_CLASSES)
+    return nullptr;
+  // the sampling decision is taken at capture; every replay of the captured launch is timed
+  if (ctx->prof_seen[cls] % ctx->prof_every != 0) return nullptr;
+  tnfem_ctx::KTimerPool* p = ctx->ktimers;
+  if (p->used >= p->cap) return nullptr;
+  const int slot = p->used++;
+  ctx->prof_timers.push_back(tnfem_ctx::ProfTimer{slot, cls, flops, bytes});
+  return p->dev + slot;
+}
+
 ProfScope::ProfScope(tnfem_ctx* c, int cls, double flops, double bytes) : ctx(c) {
   if (ctx->prof_every <= 0 || cls < 0 || cls >= TNFEM_PROF_CLASSES) return;
-  // launches captured into a graph are credited per replay by the graph; not sampled here
+  // launches captured into a graph are credited per replay by the graph and timed on the device
+  // (prof_ktimer); not bracketed by events here
   if (ctx->capturing) {
     ctx->prof_seen[cls]++;
     return;
@@ -47,6 +95,20 @@ ProfScope::~ProfScope() {
 }
 
 void prof_resolve(tnfem_ctx* ctx) {
+  if (!ctx->prof_timers.empty()) {
+    tnfem_ctx::KTimerPool* p = ctx->ktimers;
+    std::vector<KTimer> h(p->used);
+    TN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    TN_CHECK_CUDA(cudaMemcpy(h.data(), p->dev, p->used * sizeof(KTimer), cudaMemcpyDeviceToHost));
+    for (const auto& t : ctx->prof_timers) {
+      const KTimer& k = h[t.slot];
+      ctx->prof_sampled[t.cls] += k.count;
+      ctx->prof_ms[t.cls] += k.total_ns * 1e-6;
+      ctx->prof_flops[t.cls] += t.flops * k.count;
+      ctx->prof_bytes[t.cls] += t.bytes * k.count;
+    }
+    ktimers_reset(ctx);
+  }
   if (ctx->prof_pending.empty()) return;
   TN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   for (auto& ev : ctx->prof_pending) {
@@ -68,6 +130,12 @@ void prof_resolve(tnfem_ctx* ctx) {
 }
 
 void prof_release(tnfem_ctx* ctx) {
+  if (ctx->ktimers) {
+    dfree(ctx, ctx->ktimers->dev);
+    delete ctx->ktimers;
+    ctx->ktimers = nullptr;
+  }
+  ctx->prof_timers.clear();
   for (auto& ev : ctx->prof_pending) {
     cudaEventDestroy(ev.a);
     cudaEventDestroy(ev.b);
@@ -92,6 +160,14 @@ tnfem_status tnfem_profile_start(tnfem_ctx* ctx, int every) {
     return e.status;
   }
   ctx->prof_every = every > 0 ? every : 0;
+  if (ctx->prof_every > 0) {
+    try {
+      ktimers_reset(ctx);
+    } catch (const Error& e) {
+      ctx->err = e.what();
+      return e.status;
+    }
+  }
   for (int c = 0; c < TNFEM_PROF_CLASSES; ++c) {
     ctx->prof_seen[c] = ctx->prof_sampled[c] = 0;
     ctx->prof_ms[c] = ctx->prof_flops[c] = ctx->prof_bytes[c] = 0.0;
