@@ -34,14 +34,17 @@ namespace {
 
 constexpr int RT = 256;
 
-__device__ __forceinline__ double block_reduce_partials(const double* __restrict__ part, double* sh) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) s += part[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+// Sum of np per-block partials, computed by warp 0 only and broadcast through shared memory:
+// binary64 arithmetic is scarce on this part, so the block's other warps do none of it.
+__device__ __forceinline__ double block_reduce_partials(const double* __restrict__ part, int np, double* sh) {
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += 32) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) sh[0] = s;
+  }
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  const double t = sh[0];
   __syncthreads();
   return t;
 }
@@ -85,29 +88,44 @@ __global__ void __launch_bounds__(RT) cg_dot_kernel(const T* __restrict__ x, con
 
 // Stop test on r.r (partials part_rr), then alpha = r.z / pAp; x += alpha p; r -= alpha Ap;
 // partial sums of the new r.r.  Without a preconditioner z = r and part_rz aliases part_rr.
+// The three sums and alpha are formed by warp 0 and broadcast.
 // ctl[0]: 0 running, 1 converged, 2 breakdown; ctl[1]: iterations done
 template <typename T>
 __global__ void __launch_bounds__(RT) cg_update1_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                         const T* __restrict__ Ap, size_t N,
-                                                        const double* __restrict__ part_rr,
-                                                        const double* __restrict__ part_rz,
-                                                        const double* __restrict__ part_pAp,
+                                                        const double* __restrict__ part_rr, int np_rr,
+                                                        const double* __restrict__ part_rz, int np_rz,
+                                                        const double* __restrict__ part_pAp, int np_pap,
                                                         double* __restrict__ part_rr_new, int* __restrict__ ctl,
                                                         double stop2) {
   if (ctl[0]) return;
   __shared__ double sh[32];
-  const double rr = block_reduce_partials(part_rr, sh);
-  const double rz = block_reduce_partials(part_rz, sh);
-  const double pAp = block_reduce_partials(part_pAp, sh);
-  if (rr <= stop2) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl[0] = 1;
+  __shared__ double s_alpha;
+  __shared__ int s_state;
+  if (threadIdx.x < 32) {
+    double rr = 0.0, rz = 0.0, pap = 0.0;
+    for (int i = threadIdx.x; i < np_rr; i += 32) rr += part_rr[i];
+    for (int i = threadIdx.x; i < np_rz; i += 32) rz += part_rz[i];
+    for (int i = threadIdx.x; i < np_pap; i += 32) pap += part_pAp[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      rz += __shfl_xor_sync(0xffffffffu, rz, o);
+      pap += __shfl_xor_sync(0xffffffffu, pap, o);
+    }
+    if (threadIdx.x == 0) {
+      int state = 0;
+      if (rr <= stop2) state = 1;
+      else if (!(pap > 0.0) || !isfinite(pap) || !(rz > 0.0)) state = 2;
+      s_state = state;
+      s_alpha = state == 0 ? rz / pap : 0.0;
+    }
+  }
+  __syncthreads();
+  if (s_state) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl[0] = s_state;
     return;
   }
-  if (!(pAp > 0.0) || !isfinite(pAp) || !(rz > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl[0] = 2;
-    return;
-  }
-  const T alpha = (T)(rz / pAp);
+  const T alpha = (T)s_alpha;
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
@@ -123,12 +141,24 @@ __global__ void __launch_bounds__(RT) cg_update1_kernel(T* __restrict__ x, T* __
 template <typename T>
 __global__ void __launch_bounds__(RT) cg_update2_kernel(T* __restrict__ p, const T* __restrict__ z, size_t N,
                                                         const double* __restrict__ part_rz_new,
-                                                        const double* __restrict__ part_rz, const int* __restrict__ ctl) {
+                                                        const double* __restrict__ part_rz, int np_rz,
+                                                        const int* __restrict__ ctl) {
   if (ctl[0]) return;
-  __shared__ double sh[32];
-  const double rn = block_reduce_partials(part_rz_new, sh);
-  const double ro = block_reduce_partials(part_rz, sh);
-  const T beta = (T)(rn / ro);
+  __shared__ double s_beta;
+  if (threadIdx.x < 32) {
+    double rn = 0.0, ro = 0.0;
+    for (int i = threadIdx.x; i < np_rz; i += 32) {
+      rn += part_rz_new[i];
+      ro += part_rz[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      rn += __shfl_xor_sync(0xffffffffu, rn, o);
+      ro += __shfl_xor_sync(0xffffffffu, ro, o);
+    }
+    if (threadIdx.x == 0) s_beta = rn / ro;
+  }
+  __syncthreads();
+  const T beta = (T)s_beta;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
 }
@@ -168,7 +198,7 @@ __global__ void scale_rows_kernel(T* __restrict__ M, const T* __restrict__ s, in
 
 __global__ void sum_partials_kernel(const double* __restrict__ part, double* __restrict__ out) {
   __shared__ double sh[32];
-  double s = block_reduce_partials(part, sh);
+  double s = block_reduce_partials(part, kReduceBlocks, sh);
   if (threadIdx.x == 0) *out = s;
 }
 
@@ -699,9 +729,14 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
   TN_CHECK_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), ctx_->stream));
   matvec<U>(r0, n, r1, a0, a1, PL, Ak, PR, y, b.Bx, b.ws, b.wsn, nullptr);
   count_apply(r0, r1, r0, r1, n, a0, a1);
-  cg_init_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(g, b.Bx, b.r, b.p, N, prr[0]);
+  // blocks of the vector kernels: ~8 elements per thread (the vectors are short); the
+  // preconditioner works block by block over b
+  const int nb = (int)std::max<long long>(1, std::min<long long>(kReduceBlocks, ((long long)N + 2047) / 2048));
+  const int nbj = std::max(1, std::min(kReduceBlocks, r1));
+  const int np_rz = b.pre ? nbj : nb;
+  cg_init_kernel<U><<<nb, RT, 0, ctx_->stream>>>(g, b.Bx, b.r, b.p, N, prr[0]);
   count_launch(ctx_);
-  if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, b.p, prz[0], nullptr);
+  if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, b.p, prz[0], nullptr, nbj);
   const double stop2 = rtol * rtol * gnorm * gnorm;
   constexpr int kChunk = 8;  // even: the partial-sum buffers are back at index 0 after a chunk
   auto chunk = [&]() {
@@ -711,17 +746,17 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
       matvec<U>(r0, n, r1, a0, a1, PL, Ak, PR, b.p, b.Ap, b.ws, b.wsn, ctl);
       {
         ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 2.0 * N * sizeof(U));
-        cg_dot_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(b.p, b.Ap, N, ppap, ctl);
+        cg_dot_kernel<U><<<nb, RT, 0, ctx_->stream>>>(b.p, b.Ap, N, ppap, ctl);
       }
       {
         ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 6.0 * N, 6.0 * N * sizeof(U));
-        cg_update1_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(y, b.r, b.p, b.Ap, N, prr[cur], prz[cur], ppap,
-                                                                     prr[nx], ctl, stop2);
+        cg_update1_kernel<U><<<nb, RT, 0, ctx_->stream>>>(y, b.r, b.p, b.Ap, N, prr[cur], nb, prz[cur], np_rz, ppap,
+                                                          nb, prr[nx], ctl, stop2);
       }
-      if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, nullptr, prz[nx], ctl);
+      if (b.pre) bj_apply<U>(ctx_, r0, n, r1, bjP_.p, b.r, b.z, nullptr, prz[nx], ctl, nbj);
       {
         ProfScope ps(ctx_, TNFEM_PROF_KRYLOV, 2.0 * N, 3.0 * N * sizeof(U));
-        cg_update2_kernel<U><<<kReduceBlocks, RT, 0, ctx_->stream>>>(b.p, z, N, prz[nx], prz[cur], ctl);
+        cg_update2_kernel<U><<<nb, RT, 0, ctx_->stream>>>(b.p, z, N, prz[nx], prz[cur], np_rz, ctl);
       }
       count_launch(ctx_, 3);
       cur = nx;

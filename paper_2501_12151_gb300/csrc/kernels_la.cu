@@ -170,11 +170,21 @@ __global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restri
         }
         a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
         if (c == T(0) || a == T(0) || b == T(0)) continue;
-        if (fabs(c) <= tol * sqrt(a * b)) continue;
-        T zeta = (b - a) / (T(2) * c);
-        T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        T cs = T(1) / sqrt(T(1) + t * t);
-        T sn = cs * t;
+        // the rotation is computed by one lane and broadcast: square roots and divisions are long
+        // FMA sequences, and binary64 FMA throughput is scarce on this part
+        T cs = T(1), sn = T(0);
+        int rotate = 0;
+        if (lane == 0 && fabs(c) > tol * sqrt(a * b)) {
+          const T zeta = (b - a) / (T(2) * c);
+          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          cs = T(1) / sqrt(T(1) + t * t);
+          sn = cs * t;
+          rotate = 1;
+        }
+        rotate = __shfl_sync(0xffffffffu, rotate, 0);
+        if (!rotate) continue;
+        cs = __shfl_sync(0xffffffffu, cs, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
         for (int i = lane; i < m; i += 32) {
           T x = gp[i], y = gq[i];
           gp[i] = cs * x - sn * y;

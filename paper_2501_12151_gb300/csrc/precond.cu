@@ -101,26 +101,28 @@ __global__ void __launch_bounds__(PT) bj_apply_kernel(const float* __restrict__ 
                                                       T* __restrict__ z, T* __restrict__ p_out, int m, int r1,
                                                       double* __restrict__ part, const int* __restrict__ ctl) {
   if (ctl && ctl[0]) return;
-  extern __shared__ double shd[];
-  double* rb = shd;  // m values
+  // The block products run in binary32 for either precision of the solve: the preconditioner is
+  // only an approximation of B^{-1}, and binary64 FMA throughput is scarce on this part.  The r.z
+  // partials that conjugate gradients needs are accumulated in binary64 from the stored values.
+  extern __shared__ float rbf[];  // m values of this block's slice of r
   __shared__ double red[PT / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double acc_rz = 0.0;
   for (int b = blockIdx.x; b < r1; b += gridDim.x) {
     __syncthreads();
-    for (int q = threadIdx.x; q < m; q += blockDim.x) rb[q] = (double)r[(long long)q * r1 + b];
+    for (int q = threadIdx.x; q < m; q += blockDim.x) rbf[q] = (float)r[(long long)q * r1 + b];
     __syncthreads();
     const float* P = Pinv + (long long)b * m * m;
     for (int row = warp; row < m; row += PT / 32) {
       const float* pr = P + (long long)row * m;
-      double s = 0.0;
-      for (int q = lane; q < m; q += 32) s += (double)pr[q] * rb[q];
+      float s = 0.f;
+      for (int q = lane; q < m; q += 32) s = fmaf(pr[q], rbf[q], s);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
         const T zv = (T)s;
         z[(long long)row * r1 + b] = zv;
         if (p_out) p_out[(long long)row * r1 + b] = zv;
-        acc_rz += rb[row] * (double)zv;
+        acc_rz += (double)r[(long long)row * r1 + b] * (double)zv;
       }
     }
   }
@@ -191,10 +193,10 @@ bool bj_setup(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1, const T* Ph
 
 template <typename T>
 void bj_apply(tnfem_ctx* ctx, int r0, int n, int r1, const float* Pinv, const T* r, T* z, T* p_out, double* part,
-              const int* ctl) {
+              const int* ctl, int nblocks) {
   const int m = r0 * n;
   ProfScope ps(ctx, TNFEM_PROF_KRYLOV, 2.0 * r1 * (double)m * m, (double)r1 * m * m * sizeof(float));
-  bj_apply_kernel<T><<<kReduceBlocks, PT, m * sizeof(double), ctx->stream>>>(Pinv, r, z, p_out, m, r1, part, ctl);
+  bj_apply_kernel<T><<<nblocks, PT, m * sizeof(float), ctx->stream>>>(Pinv, r, z, p_out, m, r1, part, ctl);
   count_launch(ctx);
 }
 
@@ -203,8 +205,8 @@ template bool bj_setup<double>(tnfem_ctx*, int, int, int, int, int, const double
 template bool bj_setup<float>(tnfem_ctx*, int, int, int, int, int, const float*, const float*, const float*, float*,
                               float*, size_t, int*);
 template void bj_apply<double>(tnfem_ctx*, int, int, int, const float*, const double*, double*, double*, double*,
-                               const int*);
+                               const int*, int);
 template void bj_apply<float>(tnfem_ctx*, int, int, int, const float*, const float*, float*, float*, double*,
-                              const int*);
+                              const int*, int);
 
 }  // namespace tnfem
