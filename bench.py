@@ -243,7 +243,7 @@ def run_ours(args):
     lat = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ctx.launches
-    ctx.profile_start(args.prof_every)
+    ctx.profile_start(max(0, args.prof_every))
     infos = []
     with ClockSampler(local) as clk:
         barrier(world)

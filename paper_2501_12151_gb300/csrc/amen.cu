@@ -401,6 +401,8 @@ class Amen {
   DArr<double> d64_;
   long long local_refines_ = 0;
   long long breakdowns_ = 0;
+  bool init_r_ready_ = false;  // r_ holds g - B x_k of the current core step (norm init_rn_)
+  double init_rn_ = 0.0;
   ChunkGraph graph_[2];  // conjugate-gradient chunk graphs, binary32 / binary64
   TcMatvec tcmv_;        // binary32 local matvec on the tensor cores (packed operands)
   bool tcmv_on_ = false; // tcmv_ holds the current local system
@@ -857,17 +859,24 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
     } off{tcmv_on_};
     int iters = 0;
     double prev = 0.0;
+    const bool have_r0 = init_r_ready_;  // the sweep step already formed r = g - B y for this y
+    init_r_ready_ = false;
     for (int step = 0; step < 12; ++step) {
-      // binary64 residual r = g - B y
-      local_matvec<double>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, Bx_.p, wsT_.p, wsT_.n);
-      count_apply(r0, r1, r0, r1, n, a0, a1);
-      diff_kernel<double><<<kReduceBlocks, RT, 0, ctx_->stream>>>(r_.p, g, Bx_.p, N, part_.p + 5 * kReduceBlocks);
-      sum_partials_kernel<<<1, RT, 0, ctx_->stream>>>(part_.p + 5 * kReduceBlocks, d64_.p + N);
-      count_launch(ctx_, 2);
-      double rn2 = 0;
-      TN_CHECK_CUDA(cudaMemcpyAsync(&rn2, d64_.p + N, sizeof(double), cudaMemcpyDeviceToHost, ctx_->stream));
-      sync(ctx_);
-      const double rn = std::sqrt(rn2);
+      double rn;
+      if (step == 0 && have_r0) {
+        rn = init_rn_;
+      } else {
+        // binary64 residual r = g - B y
+        local_matvec<double>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, y, Bx_.p, wsT_.p, wsT_.n);
+        count_apply(r0, r1, r0, r1, n, a0, a1);
+        diff_kernel<double><<<kReduceBlocks, RT, 0, ctx_->stream>>>(r_.p, g, Bx_.p, N, part_.p + 5 * kReduceBlocks);
+        sum_partials_kernel<<<1, RT, 0, ctx_->stream>>>(part_.p + 5 * kReduceBlocks, d64_.p + N);
+        count_launch(ctx_, 2);
+        double rn2 = 0;
+        TN_CHECK_CUDA(cudaMemcpyAsync(&rn2, d64_.p + N, sizeof(double), cudaMemcpyDeviceToHost, ctx_->stream));
+        sync(ctx_);
+        rn = std::sqrt(rn2);
+      }
       if (!(rn > rtol * gnorm)) break;
       if (step > 0 && !(rn < 0.5 * prev)) break;  // stagnation: binary32 cannot reduce it further
       prev = rn;
@@ -911,6 +920,9 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   sync(ctx_);
   const double res = gnorm > 0 ? std::sqrt(rn2) / gnorm : 0.0;
   max_res_ = std::max(max_res_, res);
+  // r_ now holds g - B x_k; the binary32-local-solve path starts its refinement from it
+  init_rn_ = std::sqrt(rn2);
+  init_r_ready_ = true;
   // 3. local solve
   copy<T>(ctx_, y_.p, xk, N);
   if (res > prm_.tol / prm_.resid_damp && gnorm > 0) {

@@ -14,6 +14,7 @@ namespace {
 
 constexpr int LT = 1024;
 constexpr size_t kSvdSmemMax = 200 * 1024;  // working copies of the Jacobi SVD up to this size stay on chip
+constexpr int kSvdCoopMinN = 16;             // binary64 SVDs with at least this many columns use svd_coop_kernel
 
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
@@ -242,6 +243,150 @@ __global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restri
   }
 }
 
+// ---- multi-CTA one-sided Jacobi --------------------------------------------------------------
+// The same rotations as svd_kernel, but each pair of a round is handled by its own CTA (one warp),
+// so the binary64 work of a round is spread over as many SMs as there are pairs; rounds are
+// separated by a grid barrier.  The kernel is launched cooperatively (all CTAs resident), and
+// every barrier wait is bounded: on expiry the CTA sets err[0], and every CTA leaves at the next
+// barrier check without writing outputs.
+
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int rot[127];  // rotations per sweep (zeroed before the launch)
+};
+
+constexpr long long kBarSpin = 1ll << 24;
+
+// true when all CTAs arrived and no CTA reported an error
+__device__ bool grid_barrier(GridBar* bar) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &bar->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == g) {
+        if (++it > kBarSpin) {
+          atomicExch(&bar->err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&bar->err) == 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) svd_coop_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
+                                                      T* __restrict__ S, T* __restrict__ Vt, T* G, T* V, T* sig,
+                                                      int max_sweeps, GridBar* bar) {
+  const int lane = threadIdx.x;
+  const int cta = blockIdx.x, ncta = gridDim.x;
+  // copy-in: G column-major, V = I (rows spread over CTAs)
+  for (long long t = (long long)cta * 32 + lane; t < (long long)m * n; t += (long long)ncta * 32) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    G[(long long)j * m + i] = A[t];
+  }
+  for (long long t = (long long)cta * 32 + lane; t < (long long)n * n; t += (long long)ncta * 32) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    V[t] = (i == j) ? T(1) : T(0);
+  }
+  if (!grid_barrier(bar)) return;
+  const int np = n + (n & 1);
+  const T tol = eps_of<T>() * (T)4;
+  const int sweeps = min(max_sweeps, 127);
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      for (int pi = cta; pi < np / 2; pi += ncta) {
+        int p, q;
+        if (pi == 0) { p = r; q = np - 1; }
+        else { p = (r + pi) % (np - 1); q = (r - pi + (np - 1)) % (np - 1); }
+        if (p >= n || q >= n) continue;
+        if (p > q) { int t = p; p = q; q = t; }
+        T* gp = G + (long long)p * m;
+        T* gq = G + (long long)q * m;
+        T a = T(0), b = T(0), c = T(0);
+        for (int i = lane; i < m; i += 32) {
+          T x = gp[i], y = gq[i];
+          a += x * x; b += y * y; c += x * y;
+        }
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (c == T(0) || a == T(0) || b == T(0)) continue;
+        T cs = T(1), sn = T(0);
+        int rotate = 0;
+        if (lane == 0 && fabs(c) > tol * sqrt(a * b)) {
+          const T zeta = (b - a) / (T(2) * c);
+          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          cs = T(1) / sqrt(T(1) + t * t);
+          sn = cs * t;
+          rotate = 1;
+        }
+        rotate = __shfl_sync(0xffffffffu, rotate, 0);
+        if (!rotate) continue;
+        cs = __shfl_sync(0xffffffffu, cs, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
+        for (int i = lane; i < m; i += 32) {
+          T x = gp[i], y = gq[i];
+          gp[i] = cs * x - sn * y;
+          gq[i] = sn * x + cs * y;
+        }
+        T* vp = V + (long long)p * n;
+        T* vq = V + (long long)q * n;
+        for (int i = lane; i < n; i += 32) {
+          T x = vp[i], y = vq[i];
+          vp[i] = cs * x - sn * y;
+          vq[i] = sn * x + cs * y;
+        }
+        if (lane == 0) atomicAdd(&bar->rot[sweep], 1);
+      }
+      if (!grid_barrier(bar)) return;
+    }
+    if (*((volatile int*)&bar->rot[sweep]) == 0) break;
+  }
+  // singular values, then (after a barrier) ranks, signs and outputs; columns spread over CTAs
+  for (int j = cta; j < n; j += ncta) {
+    T s = T(0);
+    for (int i = lane; i < m; i += 32) s += G[(long long)j * m + i] * G[(long long)j * m + i];
+    s = warp_sum(s);
+    if (lane == 0) sig[j] = sqrt(s);
+  }
+  if (!grid_barrier(bar)) return;
+  for (int j = cta; j < n; j += ncta) {
+    const T sj = sig[j];
+    int pos = 0;
+    for (int i = lane; i < n; i += 32) {
+      T si = sig[i];
+      pos += (si > sj || (si == sj && i < j)) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+    T best = T(-1);
+    int bi = 0;
+    for (int i = lane; i < m; i += 32) {
+      T v = fabs(G[(long long)j * m + i]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    T sgn = (G[(long long)j * m + bi] < T(0)) ? T(-1) : T(1);
+    T inv = sj > T(0) ? sgn / sj : T(0);
+    for (int i = lane; i < m; i += 32) U[(long long)i * n + pos] = G[(long long)j * m + i] * inv;
+    for (int i = lane; i < n; i += 32) Vt[(long long)pos * n + i] = sgn * V[(long long)j * n + i];
+    if (lane == 0) S[pos] = sj;
+  }
+}
+
 }  // namespace
 
 size_t qr_work_elems(int m, int n) { return (size_t)std::min(m, n) + 8; }
@@ -264,6 +409,29 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   T* G = work;
   T* V = G + (size_t)m * n;
   T* sig = V + (size_t)n * n;
+  if (sizeof(T) == 8 && n >= kSvdCoopMinN) {
+    // binary64 with enough pairs per round: spread the rounds over SMs
+    GridBar* bar = reinterpret_cast<GridBar*>(ctx->scratch + kScratchDoubles - 512);
+    TN_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx->stream));
+    int ncta = (n + (n & 1)) / 2;
+    int dev_sms = 0;
+    TN_CHECK_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    ncta = std::max(1, std::min(ncta, dev_sms));
+    int max_sweeps = 60;
+    void* args[] = {&m, &n, &A, &U, &S, &Vt, &G, &V, &sig, &max_sweeps, &bar};
+    {
+      ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
+      TN_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(svd_coop_kernel<T>), dim3(ncta), dim3(32),
+                                                args, 0, ctx->stream));
+    }
+    count_launch(ctx);
+    check_launch(ctx, "svd");
+    int err = 0;
+    TN_CHECK_CUDA(cudaMemcpyAsync(&err, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    if (err) throw Error(TNFEM_E_TIMEOUT, "svd: a grid barrier wait expired");
+    return;
+  }
   ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
   const size_t smem = ((size_t)m * n + (size_t)n * n + n) * sizeof(T);
   const int use_smem = smem <= kSvdSmemMax ? 1 : 0;
