@@ -734,7 +734,8 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
   // blocks of the vector kernels: ~8 elements per thread (the vectors are short); the
   // preconditioner works block by block over b
   const int nb = (int)std::max<long long>(1, std::min<long long>(kReduceBlocks, ((long long)N + 2047) / 2048));
-  const int nbj = std::max(1, std::min(kReduceBlocks, r1));
+  // preconditioner apply: up to 4 CTAs per block b (rows split), at most kReduceBlocks CTAs
+  const int nbj = std::max(1, std::min(kReduceBlocks, r1 * std::max(1, std::min(4, kReduceBlocks / std::max(1, r1)))));
   const int np_rz = b.pre ? nbj : nb;
   cg_init_kernel<U><<<nb, RT, 0, ctx_->stream>>>(g, b.Bx, b.r, b.p, N, prr[0]);
   count_launch(ctx_);
@@ -923,8 +924,9 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   // r_ now holds g - B x_k; the binary32-local-solve path starts its refinement from it
   init_rn_ = std::sqrt(rn2);
   init_r_ready_ = true;
-  // 3. local solve
-  copy<T>(ctx_, y_.p, xk, N);
+  // 3. local solve (a zero projected load has the zero local solution)
+  if (gnorm > 0) copy<T>(ctx_, y_.p, xk, N);
+  else fill<T>(ctx_, y_.p, T(0), N);
   if (res > prm_.tol / prm_.resid_damp && gnorm > 0) {
     // the local system is solved to a fraction of its own starting residual (not below tol / 2):
     // the sweep's accuracy is set by the truncation, so tighter local solves only cost iterations

@@ -95,11 +95,14 @@ __global__ void __launch_bounds__(1024) bj_invert_kernel(float* __restrict__ Pb,
 }
 
 // z[(a',i)][b] = sum_q Pinv_b[(a',i)][q] r[q][b]; partial sums of r.z per CTA into part[blockIdx.x]
-// (every one of the gridDim.x entries is written); with p_out != nullptr also p = z.
+// (every one of the gridDim.x entries is written); with p_out != nullptr also p = z.  CTA c takes
+// block b = c % r1 and the row slice c / r1 of `split` equal slices, so a preconditioner block is
+// spread over `split` CTAs.
 template <typename T>
 __global__ void __launch_bounds__(PT) bj_apply_kernel(const float* __restrict__ Pinv, const T* __restrict__ r,
                                                       T* __restrict__ z, T* __restrict__ p_out, int m, int r1,
-                                                      double* __restrict__ part, const int* __restrict__ ctl) {
+                                                      int split, double* __restrict__ part,
+                                                      const int* __restrict__ ctl) {
   if (ctl && ctl[0]) return;
   // The block products run in binary32 for either precision of the solve: the preconditioner is
   // only an approximation of B^{-1}, and binary64 FMA throughput is scarce on this part.  The r.z
@@ -108,12 +111,15 @@ __global__ void __launch_bounds__(PT) bj_apply_kernel(const float* __restrict__ 
   __shared__ double red[PT / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double acc_rz = 0.0;
-  for (int b = blockIdx.x; b < r1; b += gridDim.x) {
+  const int per = (m + split - 1) / split;
+  for (int c = blockIdx.x; c < r1 * split; c += gridDim.x) {
+    const int b = c % r1, slice = c / r1;
+    const int row0 = slice * per, row1 = min(m, row0 + per);
     __syncthreads();
     for (int q = threadIdx.x; q < m; q += blockDim.x) rbf[q] = (float)r[(long long)q * r1 + b];
     __syncthreads();
     const float* P = Pinv + (long long)b * m * m;
-    for (int row = warp; row < m; row += PT / 32) {
+    for (int row = row0 + warp; row < row1; row += PT / 32) {
       const float* pr = P + (long long)row * m;
       float s = 0.f;
       for (int q = lane; q < m; q += 32) s = fmaf(pr[q], rbf[q], s);
@@ -196,7 +202,8 @@ void bj_apply(tnfem_ctx* ctx, int r0, int n, int r1, const float* Pinv, const T*
               const int* ctl, int nblocks) {
   const int m = r0 * n;
   ProfScope ps(ctx, TNFEM_PROF_KRYLOV, 2.0 * r1 * (double)m * m, (double)r1 * m * m * sizeof(float));
-  bj_apply_kernel<T><<<nblocks, PT, m * sizeof(float), ctx->stream>>>(Pinv, r, z, p_out, m, r1, part, ctl);
+  const int split = std::max(1, nblocks / std::max(1, r1));
+  bj_apply_kernel<T><<<nblocks, PT, m * sizeof(float), ctx->stream>>>(Pinv, r, z, p_out, m, r1, split, part, ctl);
   count_launch(ctx);
 }
 

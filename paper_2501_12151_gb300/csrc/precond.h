@@ -19,8 +19,9 @@ size_t bj_work_elems(int r0, int n, int r1, int a0, int a1);
 template <typename T>
 bool bj_setup(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1, const T* PhiL, const T* Ap, const T* PhiR,
               float* Pinv, T* work, size_t work_elems, int* flag);
-// z = M^{-1} r on a core [r0][n][r1] with `nblocks` CTAs (each takes blocks b in turn);
-// part[0..nblocks) receives partial sums of r.z; p_out (nullable) receives a copy of z.  Skipped
+// z = M^{-1} r on a core [r0][n][r1] with `nblocks` CTAs (nblocks / r1 CTAs share each block b
+// when nblocks >= r1, else each CTA takes blocks in turn); part[0..nblocks) receives partial
+// sums of r.z; p_out (nullable) receives a copy of z.  Skipped
 // when ctl[0] != 0 (ctl nullable).
 template <typename T>
 void bj_apply(tnfem_ctx* ctx, int r0, int n, int r1, const float* Pinv, const T* r, T* z, T* p_out, double* part,
