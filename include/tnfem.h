@@ -121,6 +121,10 @@ typedef struct {
   double flops;        /* algorithmic flops counted by the sweep's contractions */
   size_t bytes_A, bytes_f, bytes_u; /* storage of the operator, load and solution cores */
   int converged;       /* 1 when the stopping rule fired */
+  double t_phase_ms[7]; /* with the environment variable TNFEM_TRACE set: wall time per phase of
+                           the core steps (device-synchronised at phase boundaries): right-hand
+                           side projection, local residual, local solve, truncated SVD,
+                           enrichment, environment update, other; zeros otherwise */
 } tnfem_solve_info;
 
 /* ---- context ------------------------------------------------------------------------------ */

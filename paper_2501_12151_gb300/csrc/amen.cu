@@ -402,6 +402,21 @@ class Amen {
   long long local_refines_ = 0;
   long long breakdowns_ = 0;
   bool init_r_ready_ = false;  // r_ holds g - B x_k of the current core step (norm init_rn_)
+  bool last_cg_converged_ = false;  // the last conjugate-gradient run met its tolerance
+  // per-phase wall time (device-synchronised at each phase boundary when tracing is on)
+  bool trace_ = false;
+  int cur_phase_ = -1;
+  std::chrono::steady_clock::time_point phase_t0_;
+  double phase_ms_[kPhases] = {};
+  void phase(int next) {
+    if (!trace_) return;
+    sync(ctx_);
+    const auto now = std::chrono::steady_clock::now();
+    if (cur_phase_ >= 0) phase_ms_[cur_phase_] += std::chrono::duration<double, std::milli>(now - phase_t0_).count();
+    cur_phase_ = next;
+    phase_t0_ = now;
+  }
+  long long fallbacks_ = 0;          // binary32 local solves finished in binary64
   double init_rn_ = 0.0;
   ChunkGraph graph_[2];  // conjugate-gradient chunk graphs, binary32 / binary64
   TcMatvec tcmv_;        // binary32 local matvec on the tensor cores (packed operands)
@@ -780,6 +795,7 @@ int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U
     TN_CHECK_CUDA(cudaMemcpyAsync(h, ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx_->stream));
     sync(ctx_);
     done_it = h[1];
+    last_cg_converged_ = h[0] == 1;
     if (h[0] == 2) {
       // Loss of positive curvature (rounding in a binary32 solve of an ill-conditioned system):
       // the iterate of the last completed step is kept and the sweep carries on.
@@ -862,6 +878,7 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
     double prev = 0.0;
     const bool have_r0 = init_r_ready_;  // the sweep step already formed r = g - B y for this y
     init_r_ready_ = false;
+    bool stalled = false;
     for (int step = 0; step < 12; ++step) {
       double rn;
       if (step == 0 && have_r0) {
@@ -879,7 +896,10 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
         rn = std::sqrt(rn2);
       }
       if (!(rn > rtol * gnorm)) break;
-      if (step > 0 && !(rn < 0.5 * prev)) break;  // stagnation: binary32 cannot reduce it further
+      if (step > 0 && !(rn < 0.5 * prev)) {  // stagnation: binary32 cannot reduce it further
+        stalled = true;
+        break;
+      }
       prev = rn;
       ++local_refines_;
       // d solves B d = r / ||r|| in binary32 to the reduction still needed (not below 1e-6)
@@ -891,6 +911,14 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
                               std::max(1e-6, 0.5 * need), b);
       add_scaled_float_kernel<<<nblk((long long)N), RT, 0, ctx_->stream>>>(y, y32_.p, rn, N);
       count_launch(ctx_);
+    }
+    if (stalled) {
+      // binary32 cannot reduce this system's residual any further (its conditioning exceeds what
+      // binary32 products resolve): finish the local solve in binary64 from the current y
+      ++fallbacks_;
+      const bool pre64 = setup_pre<double>(r0, n, r1, a0, a1, PL, Ak, PR, bjw_);
+      CgBufs<double> b64{Bx_.p, r_.p, p_.p, Ap_.p, z_.p, wsT_.p, wsT_.n, pre64};
+      iters += pcg_run<double>(r0, n, r1, a0, a1, PL, Ak, PR, y, g, gnorm, rtol, b64);
     }
     check_tc_error();
     return iters;
@@ -907,10 +935,12 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   T* xk = xc_[slot];
   const T* Ak = Acur(k);
   // 1. projected right-hand side
+  phase(kPhaseRhs);
   source_proj(k, false, false, g64_.p, r0, r1);
   convert_any<double, T>(ctx_, g_.p, g64_.p, N);
   const double gnorm = nrm2<double>(ctx_, g64_.p, N);
   // 2. local residual before the solve
+  phase(kPhaseResidual);
   local_matvec<T>(ctx_, r0, n, r1, a0, a1, EL(0, k), Ak, ER(0, k), xk, Bx_.p, wsT_.p, wsT_.n);
   count_apply(r0, r1, r0, r1, n, a0, a1);
   diff_kernel<T><<<kReduceBlocks, RT, 0, ctx_->stream>>>(r_.p, g_.p, Bx_.p, N, part_.p);
@@ -925,6 +955,7 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   init_rn_ = std::sqrt(rn2);
   init_r_ready_ = true;
   // 3. local solve (a zero projected load has the zero local solution)
+  phase(kPhaseSolve);
   if (gnorm > 0) copy<T>(ctx_, y_.p, xk, N);
   else fill<T>(ctx_, y_.p, T(0), N);
   if (res > prm_.tol / prm_.resid_damp && gnorm > 0) {
@@ -946,6 +977,7 @@ void Amen<T>::core_step(int k, AmenStats& st) {
     return;
   }
   // 4. truncated SVD of y as (r0 n) x r1
+  phase(kPhaseSvd);
   const int m = r0 * n;
   int p;
   if (m >= r1) {
@@ -982,6 +1014,7 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   int kq = rk;
   T* Vnew = Vt_.p;  // kq x r1
   if (kick > 0) {
+    phase(kPhaseEnrich);
     // yt = U_rk V (m x r1)
     GemmDesc gy{m, r1, rk, 1, ue_cols, 1, 0, r1, 1, 0, r1, 1, 0};
     gemm<T>(ctx_, gy, T(1), Ue_.p, Vt_.p, T(0), y_.p);
@@ -1029,6 +1062,7 @@ void Amen<T>::core_step(int k, AmenStats& st) {
     copy<T>(ctx_, xk, Ue_.p, (size_t)m * rk);
   }
   // 6. x_{k+1} <- Vnew x_{k+1}
+  phase(kPhaseEnv);
   const int nslot = oc(k + 1);
   const int n2 = ncur(k + 1), r2 = rx_[k + 2];
   TN_REQUIRE((size_t)kq * n2 * r2 <= xcap_[nslot], "next core exceeds capacity");
@@ -1043,6 +1077,7 @@ template <typename T>
 void Amen<T>::run(AmenStats& st) {
   const int d = d_;
   st = AmenStats();
+  trace_ = getenv("TNFEM_TRACE") != nullptr;
   for (int sweep = 0; sweep < prm_.max_sweeps; ++sweep) {
     max_res_ = 0.0;
     max_dx_ = 0.0;
@@ -1051,15 +1086,18 @@ void Amen<T>::run(AmenStats& st) {
     st.max_res = max_res_;
     st.max_dx = max_dx_;
     if (prm_.verbose)
-      fprintf(stderr, "[tnfem] sweep %d: max res %.3e max dx %.3e rank %d iters %lld\n", sweep, max_res_, max_dx_,
-              *std::max_element(rx_.begin(), rx_.end()), iters_);
+      fprintf(stderr, "[tnfem] sweep %d: max res %.3e max dx %.3e rank %d iters %lld refines %lld fallbacks %lld\n",
+              sweep, max_res_, max_dx_, *std::max_element(rx_.begin(), rx_.end()), iters_, local_refines_, fallbacks_);
     flip();
     if (max_res_ <= prm_.tol || max_dx_ <= prm_.tol) {
       st.converged = true;
       break;
     }
   }
+  phase(kPhaseOther);
   if (o_ == 1) flip();
+  phase(-1);
+  for (int i = 0; i < kPhases; ++i) st.phase_ms[i] = phase_ms_[i];
   st.local_iters = iters_;
   st.flops = flops_;
   st.max_rank = *std::max_element(rx_.begin(), rx_.end());

@@ -30,6 +30,18 @@ struct AmenParams {
   bool verbose = false;
 };
 
+// Phases of a core step timed when TNFEM_TRACE is set (see tnfem_solve_info.t_phase_ms).
+enum {
+  kPhaseRhs = 0,       // projection of the right-hand side onto the interfaces
+  kPhaseResidual = 1,  // local residual before the solve
+  kPhaseSolve = 2,     // local solve (preconditioner set-up, conjugate gradients, refinement)
+  kPhaseSvd = 3,       // truncated SVD
+  kPhaseEnrich = 4,    // residual projections, z update, QR of the enriched basis
+  kPhaseEnv = 5,       // next-core update and environment contractions
+  kPhaseOther = 6,     // orientation flips and bookkeeping
+  kPhases = 7
+};
+
 struct AmenStats {
   int sweeps = 0;
   int max_rank = 0;
@@ -38,6 +50,7 @@ struct AmenStats {
   double max_res = 0, max_dx = 0;
   double flops = 0;
   bool converged = false;
+  double phase_ms[kPhases] = {};
 };
 
 // Solve A x = b; `single` selects binary32 for the sweep (sources stay binary64).

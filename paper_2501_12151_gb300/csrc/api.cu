@@ -404,6 +404,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
         info->max_res = s.max_res;
         info->max_dx = s.max_dx;
         info->flops = s.flops;
+        for (int i = 0; i < 7; ++i) info->t_phase_ms[i] = s.phase_ms[i];
       }
     } else {
       res = mixed_solve(ctx, A, f, opts, x0, info, converged);

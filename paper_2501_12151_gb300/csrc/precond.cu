@@ -25,6 +25,7 @@ namespace tnfem {
 namespace {
 
 constexpr int PT = 256;
+constexpr size_t kInvertSmemMax = 220 * 1024;  // blocks up to this size are inverted in shared memory
 
 // dR[b][g] = PhiR[b][g][b]
 template <typename T>
@@ -56,12 +57,20 @@ __global__ void bj_gather_kernel(float* __restrict__ Pb, const T* __restrict__ P
 
 // In-place Gauss-Jordan inversion of the m x m block blockIdx.x (SPD, no pivoting).  A pivot
 // that is not positive marks the block as failed in flag[0]; its contents are then meaningless
-// and the caller does not use the preconditioner.
-__global__ void __launch_bounds__(1024) bj_invert_kernel(float* __restrict__ Pb, int m, int* __restrict__ flag) {
+// and the caller does not use the preconditioner.  With `in_smem` the block is copied into shared
+// memory for the elimination and written back at the end.
+__global__ void __launch_bounds__(1024) bj_invert_kernel(float* __restrict__ Pb, int m, int* __restrict__ flag,
+                                                         int in_smem) {
   extern __shared__ float sh[];
   float* col = sh;       // column k before the step
   float* rowk = sh + m;  // row k after scaling
-  float* M = Pb + (long long)blockIdx.x * m * m;
+  float* Mg = Pb + (long long)blockIdx.x * m * m;
+  float* M = in_smem ? sh + 2 * m : Mg;
+  const long long mm = (long long)m * m;
+  if (in_smem) {
+    for (long long t = threadIdx.x; t < mm; t += blockDim.x) M[t] = Mg[t];
+    __syncthreads();
+  }
   __shared__ float s_p;
   for (int k = 0; k < m; ++k) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = M[(long long)i * m + k];
@@ -83,14 +92,23 @@ __global__ void __launch_bounds__(1024) bj_invert_kernel(float* __restrict__ Pb,
       M[(long long)k * m + j] = v;
     }
     __syncthreads();
-    const long long mm = (long long)m * m;
+    // rows i != k: M[i][j] = (j == k ? 0 : M[i][j]) - col[i] rowk[j]; threads walk (i, j) with
+    // j fastest, stepping i and j incrementally
+    int i = threadIdx.x / m, j = threadIdx.x % m;
+    const int di = blockDim.x / m, dj = blockDim.x % m;
     for (long long t = threadIdx.x; t < mm; t += blockDim.x) {
-      const int i = (int)(t / m), j = (int)(t % m);
-      if (i == k) continue;
-      const float old = (j == k) ? 0.0f : M[t];
-      M[t] = old - col[i] * rowk[j];
+      if (i != k) {
+        const float old = (j == k) ? 0.0f : M[t];
+        M[t] = old - col[i] * rowk[j];
+      }
+      i += di;
+      j += dj;
+      if (j >= m) { j -= m; ++i; }
     }
     __syncthreads();
+  }
+  if (in_smem) {
+    for (long long t = threadIdx.x; t < mm; t += blockDim.x) Mg[t] = M[t];
   }
 }
 
@@ -186,8 +204,18 @@ bool bj_setup(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1, const T* Ph
   }
   TN_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
   {
+    // the block stays on chip for the elimination when it fits
+    const size_t smem_full = ((size_t)m * m + 2 * m) * sizeof(float);
+    const int in_smem = smem_full <= kInvertSmemMax ? 1 : 0;
+    static unsigned long long attr_set = 0;  // one bit per device
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (in_smem && !(attr_set & bit)) {
+      TN_CHECK_CUDA(cudaFuncSetAttribute(bj_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kInvertSmemMax));
+      attr_set |= bit;
+    }
     ProfScope ps(ctx, TNFEM_PROF_OTHER, 2.0 * r1 * (double)m * m * m, (double)total * sizeof(float));
-    bj_invert_kernel<<<r1, 1024, 2 * m * sizeof(float), ctx->stream>>>(Pinv, m, flag);
+    bj_invert_kernel<<<r1, 1024, in_smem ? smem_full : 2 * m * sizeof(float), ctx->stream>>>(Pinv, m, flag, in_smem);
     count_launch(ctx);
   }
   check_launch(ctx, "block-Jacobi set-up");

@@ -56,10 +56,15 @@ class CInfo(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("refines", C.c_int), ("max_rank", C.c_int), ("local_iters", C.c_longlong),
                 ("max_res", C.c_double), ("max_dx", C.c_double), ("energy_err_est", C.c_double),
                 ("t_solve_ms", C.c_double), ("flops", C.c_double), ("bytes_A", C.c_size_t),
-                ("bytes_f", C.c_size_t), ("bytes_u", C.c_size_t), ("converged", C.c_int)]
+                ("bytes_f", C.c_size_t), ("bytes_u", C.c_size_t), ("converged", C.c_int),
+                ("t_phase_ms", C.c_double * 7)]
+
+    PHASES = ("rhs", "residual", "solve", "svd", "enrich", "env", "other")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_phase_ms"}
+        d["t_phase_ms"] = dict(zip(self.PHASES, list(self.t_phase_ms)))
+        return d
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -209,6 +209,20 @@ def cantilever_3d(levels: int = 7, rank_cap: int = 96, tol: float = 1e-8, seed: 
     )
 
 
+def cantilever_paper_2d(levels: int = 8, rank_cap: int = 64, tol: float = 1e-10,
+                        precision: str = "fp64") -> Problem:
+    """The results section's workload: an aluminium cantilever 20 m long and 1 m high, plane
+    stress, E = 68 GPa, nu = 0.33, density 2700 kg/m^3 under its own weight, clamped at x = 0."""
+    return Problem(
+        name=f"2d-cantilever-paper-L{levels}",
+        grid=Grid(dim=2, levels=levels, lo=(0.0, 0.0, 0.0), hi=(20.0, 1.0, 0.0),
+                  clamped=(True, False, False, False, False, False), plane_stress=True),
+        material=Material(E=(68e9, 68e9), nu=0.33),
+        loads=[Load(kind="gravity", rho=2700.0)],
+        opts=SolveOpts(tol=tol, rank_cap=rank_cap, precision=precision),
+    )
+
+
 def served_requests(seed: int = 0, n: int = 512, rate: float = 200.0):
     """Mixed request stream: per request, dimension, levels, material, load and rank cap."""
     arrivals = poisson_arrivals(seed, n, rate)
