@@ -1078,6 +1078,7 @@ void Amen<T>::run(AmenStats& st) {
   const int d = d_;
   st = AmenStats();
   trace_ = getenv("TNFEM_TRACE") != nullptr;
+  double res_hist[2] = {0.0, 0.0};  // largest local residuals of the two previous sweeps
   for (int sweep = 0; sweep < prm_.max_sweeps; ++sweep) {
     max_res_ = 0.0;
     max_dx_ = 0.0;
@@ -1093,6 +1094,16 @@ void Amen<T>::run(AmenStats& st) {
       st.converged = true;
       break;
     }
+    // Stagnation at the truncation floor: the local residuals no longer fall (the SVD truncation
+    // re-creates them every step) and the core updates are within a small factor of tol, so more
+    // sweeps would only move the iterate by amounts of the order of the truncation itself.
+    if (sweep >= 2 && max_dx_ <= prm_.stall_dx * prm_.tol &&
+        max_res_ >= 0.5 * std::min(res_hist[0], res_hist[1])) {
+      st.converged = true;
+      break;
+    }
+    res_hist[0] = res_hist[1];
+    res_hist[1] = max_res_;
   }
   phase(kPhaseOther);
   if (o_ == 1) flip();
