@@ -1022,8 +1022,21 @@ void Amen<T>::core_step(int k, AmenStats& st) {
     // crs = PhiL A PhiZR yt - b projected on (x left, z right)   (r0 x n x rz1)
     source_proj(k, false, true, c64_.p, r0, rz1);
     convert_any<double, T>(ctx_, crs_.p, c64_.p, (size_t)r0 * n * rz1);
-    local_apply<T>(ctx_, r0, rz1, r0, r1, n, a0, a1, EL(0, k), Ak, ER(1, k), y_.p, crs_.p, T(1), T(-1), wsT_.p,
-                   wsT_.n);
+    if (4 * rz1 <= r1) {
+      // the right interface is narrow (kickrank columns): contract it first by applying the flipped
+      // operator core to the transposed train, y^T[b',i,a'] = PhiZR A^T PhiL x^T, which costs
+      // O(r^2 a (n + a) rz) instead of the O(r^2 n^2 a^2) of the left-first order
+      T* xt = tmpA_.p;
+      T* yt2 = tmpB_.p;
+      transpose3<T>(ctx_, xt, y_.p, r0, n, r1);  // [r1][n][r0]
+      const T* Af = Prec<T>::A(A_, o_ ^ 1, d - 1 - k);
+      local_apply<T>(ctx_, rz1, r0, r1, r0, n, a1, a0, ER(1, k), Af, EL(0, k), xt, yt2, T(1), T(0), wsT_.p, wsT_.n);
+      transpose3<T>(ctx_, xt, yt2, rz1, n, r0);  // [r0][n][rz1]
+      axpby<T>(ctx_, crs_.p, T(1), xt, T(-1), (size_t)r0 * n * rz1);
+    } else {
+      local_apply<T>(ctx_, r0, rz1, r0, r1, n, a0, a1, EL(0, k), Ak, ER(1, k), y_.p, crs_.p, T(1), T(-1), wsT_.p,
+                     wsT_.n);
+    }
     count_apply(r0, rz1, r0, r1, n, a0, a1);
     // crz = PhiZL A PhiZR yt - b projected on z's interfaces   (z0 x n x rz1)
     source_proj(k, true, true, c64_.p, z0, rz1);

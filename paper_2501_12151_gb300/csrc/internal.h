@@ -93,7 +93,7 @@ inline void count_launch(tnfem_ctx* ctx, int n = 1) { ctx->launches += n; }
 struct ProfScope {
   tnfem_ctx* ctx;
   int idx = -1;
-  ProfScope(tnfem_ctx* c, int cls, double flops, double bytes);
+  ProfScope(tnfem_ctx* c, int cls, double flops, double bytes, bool device_timed = false);
   ~ProfScope();
 };
 

@@ -325,7 +325,7 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
     const double words = ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N) * g.batch;
     const int cls = sizeof(T) == 8 ? TNFEM_PROF_CONTRACT64 : TNFEM_PROF_CONTRACT32;
     KTimer* timer = prof_ktimer(ctx, cls, 2.0 * mnk, words * sizeof(T));
-    ProfScope ps(ctx, cls, 2.0 * mnk, words * sizeof(T));
+    ProfScope ps(ctx, cls, 2.0 * mnk, words * sizeof(T), timer != nullptr);
     gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip, timer);
   }
   count_launch(ctx);

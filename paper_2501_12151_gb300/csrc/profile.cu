@@ -58,19 +58,27 @@ void ktimers_reset(tnfem_ctx* ctx) {
 }
 
 KTimer* prof_ktimer(tnfem_ctx* ctx, int cls, double flops, double bytes) {
-  if (ctx->prof_every <= 0 || !ctx->capturing || !ctx->ktimers || cls < 0 || cls >= TNFEM_PROF_CLASSES)
-    return nullptr;
-  // the sampling decision is taken at capture; every replay of the captured launch is timed
+  if (ctx->prof_every <= 0 || !ctx->ktimers || cls < 0 || cls >= TNFEM_PROF_CLASSES) return nullptr;
+  // the sampling decision is taken when the launch is issued (or captured: then every replay of
+  // the captured launch is timed); outside graphs the sampled launch is timed on the device too,
+  // so host launch gaps never enter its duration
   if (ctx->prof_seen[cls] % ctx->prof_every != 0) return nullptr;
   tnfem_ctx::KTimerPool* p = ctx->ktimers;
-  if (p->used >= p->cap) return nullptr;
+  if (p->used >= p->cap) {
+    if (ctx->capturing) return nullptr;
+    prof_resolve(ctx);  // read and recycle the slots (outside capture only)
+  }
   const int slot = p->used++;
   ctx->prof_timers.push_back(tnfem_ctx::ProfTimer{slot, cls, flops, bytes});
   return p->dev + slot;
 }
 
-ProfScope::ProfScope(tnfem_ctx* c, int cls, double flops, double bytes) : ctx(c) {
+ProfScope::ProfScope(tnfem_ctx* c, int cls, double flops, double bytes, bool device_timed) : ctx(c) {
   if (ctx->prof_every <= 0 || cls < 0 || cls >= TNFEM_PROF_CLASSES) return;
+  if (device_timed) {  // the kernel times itself (KTimer); only count the launch
+    ctx->prof_seen[cls]++;
+    return;
+  }
   // launches captured into a graph are credited per replay by the graph and timed on the device
   // (prof_ktimer); not bracketed by events here
   if (ctx->capturing) {
