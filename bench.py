@@ -319,12 +319,14 @@ def run_ours(args):
         q = prof[c]
         return q["launches"] * (q["ms"] / q["sampled"]) if q["sampled"] else 0.0
 
-    cls = max(("contract32", "contract64"), key=device_ms)
+    kernels = {"contract32": "gemm_kernel<float>", "contract64": "gemm_kernel<double>",
+               "cg32": "fcg_kernel<float>", "cg64": "fcg_kernel<double>"}
+    cls = max(kernels, key=device_ms)
     p = prof[cls]
     achieved = (p["flops"] / (p["ms"] * 1e-3) * 1e-12) if p["ms"] > 0 else 0.0
-    if cls == "contract32":
+    if cls in ("contract32", "cg32"):
         peak = fp32_simt_peak_gflops() * 1e-3
-        peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (CUDA-core binary32 GEMM)"
+        peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (CUDA-core binary32 FMA)"
     else:
         peak = FP64_NOMINAL_GFLOPS * 1e-3
         peak_note = "nominal GB300 binary64 rate (1.25 TFLOP/s; measured FMA peak alongside)"
@@ -336,16 +338,16 @@ def run_ours(args):
     measured_fma = {"fp64": ctx.fma_peak("fp64"), "fp32": ctx.fma_peak("fp32")}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
-                "kernel": "gemm_kernel<float>" if cls == "contract32" else "gemm_kernel<double>",
+                "kernel": kernels[cls],
                 "peak_source": peak_note,
                 "fma_peak_measured_tflops": measured_fma,
                 "launches": p["launches"], "sampled_launches": p["sampled"],
                 "avg_launch_us": (p["ms"] * 1e3 / p["sampled"]) if p["sampled"] else None,
                 "flops_per_launch": (p["flops"] / p["sampled"]) if p["sampled"] else None,
                 "timing": "device globaltimer per sampled GEMM launch (inside and outside CUDA graphs); "
-                          "CUDA events for the other classes",
+                          "CUDA events around each sampled fused-CG launch and the other classes",
                 "class": cls,
-                "device_ms_by_contraction_class": {c: device_ms(c) for c in ("contract32", "contract64")},
+                "device_ms_by_class": {c: device_ms(c) for c in kernels},
                 "by_class": by_class}
 
     cpu = None
@@ -432,7 +434,7 @@ def run_reference(args):
 def run_kernel_probe(args):
     """A few launches of each local-matvec engine at the solve's working shapes (for ncu): the
     binary32 contraction on CUDA cores and on the tcgen05 tensor cores, and the binary64 one,
-    through the C ABI on seeded Gaussian inputs.  Prints wall time per call (allocation and launch
+    through the C ABI on seeded Gaussian inputs; then the fused CG kernel in both precisions.  Prints wall time per call (allocation and launch
     overheads included; kernel durations come from the profiler)."""
     import numpy as np
     import torch
@@ -465,6 +467,31 @@ def run_kernel_probe(args):
                 torch.cuda.synchronize()
                 walls.append(time.perf_counter() - t0)
             out[f"{name}_engine{e if e is not None else 'fp64'}_wall_us"] = 1e6 * min(walls)
+    # the fused CG kernel on a symmetric positive definite system of the same shape
+    # (B = sum_beta PhiL_beta (x) M_beta (x) PhiR_beta, PSD factors, identity-shifted beta = 0 term),
+    # a fixed number of steps (rtol 0)
+    rs = W.rng(5)
+    SL, SA, SR = np.zeros((r0, a0, r0)), np.zeros((a0, n, n, a1)), np.zeros((r1, a1, r1))
+    for b in range(min(a0, a1)):
+        Lb, Rb, Mb = rs.standard_normal((r0, r0)), rs.standard_normal((r1, r1)), rs.standard_normal((n, n))
+        sh = 1.0 if b == 0 else 0.0
+        SL[:, b, :] = Lb @ Lb.T / r0 + sh * np.eye(r0)
+        SR[:, b, :] = Rb @ Rb.T / r1 + sh * np.eye(r1)
+        SA[b, :, :, b] = Mb @ Mb.T / n + sh * np.eye(n)
+    g = rs.standard_normal((r0, n, r1))
+    for dt, name in ((np.float32, "f32"), (np.float64, "f64")):
+        t = [dev(v, dt) for v in (SL, SA, SR, g)]
+        walls = []
+        for _ in range(args.probe_reps):
+            xg = torch.zeros(r0 * n * r1, dtype=t[0].dtype, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its, _ = ctx.op_local_cg("fp64" if dt == np.float64 else "fp32", 1, r0, n, r1, a0, a1,
+                                     *[v.data_ptr() for v in t], xg.data_ptr(), 0.0, args.probe_cg_steps)
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+        out[f"{name}_fused_cg_steps"] = its
+        out[f"{name}_fused_cg_wall_us"] = 1e6 * min(walls)
     return out
 
 
@@ -476,7 +503,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=10)
     ap.add_argument("--rank-cap", type=int, default=64)
-    ap.add_argument("--precision", choices=["mixed", "mixed-local", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "mixed-local", "fp64"], default="mixed-local")
     ap.add_argument("--tensor-cores", action="store_true", help="binary32 contractions on tcgen05")
     ap.add_argument("--prof-every", type=int, default=8, help="time every n-th launch of each kernel class")
     ap.add_argument("--fp64-steps", type=int, default=1)
@@ -485,9 +512,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--kernel-probe", action="store_true",
-                    help="only launch the local-matvec engines a few times at --probe-shape (for ncu)")
+                    help="only launch the local-matvec engines and the fused CG kernel a few times at --probe-shape (for ncu)")
     ap.add_argument("--probe-shape", type=int, nargs=5, default=[49, 4, 49, 51, 51], metavar=("R0", "N", "R1", "A0", "A1"))
     ap.add_argument("--probe-reps", type=int, default=3)
+    ap.add_argument("--probe-cg-steps", type=int, default=50, help="steps of the fused CG launch in the probe")
     args = ap.parse_args(argv)
     if args.kernel_probe:
         out = run_kernel_probe(args)

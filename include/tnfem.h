@@ -107,6 +107,8 @@ typedef struct {
   double local_rtol;   /* each local solve stops at max(tol / 2, local_rtol * its starting relative
                           residual); 0 solves every local system to tol / 2.  Default 1e-2 when the
                           field is negative */
+  int cg_engine;       /* local solves: 0 one persistent cooperative kernel per solve (default),
+                          1 one launch per conjugate-gradient step (graph-replayed chunks) */
 } tnfem_solve_opts;
 
 typedef struct {
@@ -147,14 +149,18 @@ long long tnfem_kernel_launches(const tnfem_ctx* ctx);
 
 /* ---- sampled kernel timing (tracing; not part of the method) ------------------------------ *
  * Kernel classes: the sweep's dense contractions (local matvec, environments, projections) in
- * binary32 and in binary64, the Krylov vector kernels, Householder QR, Jacobi SVD, the rest.  */
+ * binary32 and in binary64, the Krylov vector kernels, Householder QR, Jacobi SVD, the rest, and
+ * the fused conjugate-gradient kernel in binary32 and in binary64 (one launch per local solve;
+ * its flops are the local matvecs and preconditioner applies of the iterations it ran).  */
 #define TNFEM_PROF_CONTRACT32 0
 #define TNFEM_PROF_CONTRACT64 1
 #define TNFEM_PROF_KRYLOV 2
 #define TNFEM_PROF_QR 3
 #define TNFEM_PROF_SVD 4
 #define TNFEM_PROF_OTHER 5
-#define TNFEM_PROF_CLASSES 6
+#define TNFEM_PROF_CG32 6
+#define TNFEM_PROF_CG64 7
+#define TNFEM_PROF_CLASSES 8
 /* Start (or restart) sampling: from now on every `every`-th launch of each class is bracketed by
  * two CUDA events on the context's stream; every <= 0 stops sampling.  Counters are reset. */
 tnfem_status tnfem_profile_start(tnfem_ctx* ctx, int every);
@@ -297,6 +303,23 @@ tnfem_status tnfem_op_env_left(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx
 tnfem_status tnfem_op_local_matvec_noalloc(void* stream, int r0, int n, int r1, int a0, int a1,
                                            const double* PhiL, const double* A, const double* PhiR,
                                            const double* x, double* y);
+/* a5: preconditioned conjugate gradients on one local system B x = g, B the local matrix of
+ * tnfem_op_local_matvec (symmetric positive definite for the sweep's systems), run as the solver
+ * runs it: one persistent cooperative kernel for the whole iteration (three grid barriers per
+ * step; the block-Jacobi preconditioner of precond.cu when precond = 1, plain CG when 0).
+ *  - precision: TNFEM_FP64 for binary64 operands and vectors, any other value for binary32 (the
+ *    local solves of MIXED / MIXED_LOCAL); every pointer is a device pointer to that type.
+ *  - PhiL [r0][a0][r0], A [a0][n][n][a1], PhiR [r1][a1][r1], g and x [r0][n][r1]; x holds the
+ *    start guess on entry and the last iterate on return.  Mode size n <= 8.
+ *  - Stops when the recursively updated residual meets ||r|| <= rtol ||g|| or after maxit >= 0
+ *    steps.  *iters: steps done; *state: 1 converged, 0 step limit, 2 loss of positive curvature
+ *    (x holds the last completed iterate).
+ *  - TNFEM_E_INVALID: null pointer, size < 1, n > 8, a shape whose CTAs cannot all be resident, or
+ *    (precond = 1) a block of the preconditioner that is not positive definite; TNFEM_E_TIMEOUT:
+ *    a grid barrier wait expired (2 s). */
+tnfem_status tnfem_op_local_cg(tnfem_ctx* ctx, int precision, int precond, int r0, int n, int r1, int a0,
+                               int a1, const void* PhiL, const void* A, const void* PhiR, const void* g,
+                               void* x, double rtol, int maxit, int* iters, int* state);
 /* Binary32 building blocks of the mixed-precision local solves (parity tests of both engines).
  * engine 0: CUDA-core FMA; engine 1: tcgen05 tensor cores, kind::tf32 with the three-term split
  * a b = a_hi b_hi + a_hi b_lo + a_lo b_hi (binary32-level accuracy from TF32 products), operands

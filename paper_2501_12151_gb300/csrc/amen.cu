@@ -23,6 +23,7 @@
 #include <memory>
 
 #include "amen.h"
+#include "cg_fused.h"
 #include "internal.h"
 #include "precond.h"
 #include "tc_gemm.h"
@@ -419,6 +420,7 @@ class Amen {
   long long fallbacks_ = 0;          // binary32 local solves finished in binary64
   double init_rn_ = 0.0;
   ChunkGraph graph_[2];  // conjugate-gradient chunk graphs, binary32 / binary64
+  FusedCg fcg_;          // the conjugate-gradient loop as one persistent kernel
   TcMatvec tcmv_;        // binary32 local matvec on the tensor cores (packed operands)
   bool tcmv_on_ = false; // tcmv_ holds the current local system
   // local matvec of the current local system in precision U
@@ -737,6 +739,30 @@ template <typename U>
 int Amen<T>::pcg_run(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, U* y,
                      const U* g, double gnorm, double rtol, const CgBufs<U>& b) {
   const size_t N = (size_t)r0 * n * r1;
+  const bool tc_mv = std::is_same<U, float>::value && tcmv_on_;
+  if (prm_.fused_cg && !tc_mv) {
+    // the whole preconditioned CG loop as one persistent cooperative kernel
+    const FcgPlan pl = fcg_.plan<U>(ctx_, r0, n, r1, a0, a1, b.pre);
+    if (pl.ok) {
+      int state = 0;
+      const double stop2 = rtol * rtol * gnorm * gnorm;
+      const int done = fcg_.run<U>(ctx_, pl, r0, n, r1, a0, a1, PL, Ak, PR, b.pre ? bjP_.p : nullptr, g, y, stop2,
+                                   prm_.local_maxit, &state);
+      last_cg_converged_ = state == 1;
+      for (int i = 0; i <= done; ++i) count_apply(r0, r1, r0, r1, n, a0, a1);
+      if (state == 2) {
+        // Loss of positive curvature (rounding in a binary32 solve of an ill-conditioned system):
+        // the iterate of the last completed step is kept and the sweep carries on.
+        ++breakdowns_;
+        if (b.pre && done < 2) {
+          CgBufs<U> plain = b;
+          plain.pre = false;
+          return done + pcg_run<U>(r0, n, r1, a0, a1, PL, Ak, PR, y, g, gnorm, rtol, plain);
+        }
+      }
+      return done;
+    }
+  }
   double* prr[2] = {part_.p, part_.p + kReduceBlocks};
   double* prz_b[2] = {part_.p + 2 * kReduceBlocks, part_.p + 3 * kReduceBlocks};
   double* ppap = part_.p + 4 * kReduceBlocks;

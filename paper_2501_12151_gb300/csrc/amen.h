@@ -26,6 +26,7 @@ struct AmenParams {
   bool precond = true;      // block-Jacobi preconditioned conjugate gradients for the local solves
   bool local_mixed = false; // binary64 sweep with binary32 local solves refined in binary64
   bool graphs = true;       // replay the conjugate-gradient chunks as CUDA graphs
+  bool fused_cg = true;     // local CG as one persistent cooperative kernel where the shape fits
   double stall_dx = 4.0;    // stop when updates are within stall_dx * tol and residuals stagnate
   uint64_t seed = 0;
   bool verbose = false;

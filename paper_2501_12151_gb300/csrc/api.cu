@@ -7,6 +7,8 @@
 
 #include "amen.h"
 #include "builder.h"
+#include "cg_fused.h"
+#include "precond.h"
 #include "internal.h"
 #include "tc_gemm.h"
 #include "tc_matvec.h"
@@ -174,6 +176,7 @@ tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, con
   ip.seed = o->seed;
   ip.precond = o->no_precond == 0;
   ip.local_rtol = o->local_rtol < 0 ? 1e-2 : o->local_rtol;
+  ip.fused_cg = o->cg_engine == 0;
   ip.verbose = getenv("TNFEM_VERBOSE") != nullptr;
   tnfem_tt* u = x0 ? tt_clone(x0) : nullptr;
   const double fnorm = energy_norm(ctx, A, f, nullptr);  // scale reference (any norm works)
@@ -228,6 +231,34 @@ tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, con
 }
 
 }  // namespace
+
+namespace tnfem {
+
+// fused local CG of tnfem_op_local_cg in precision U
+template <typename U>
+void op_local_cg(tnfem_ctx* ctx, int precond, int r0, int n, int r1, int a0, int a1, const U* PhiL, const U* A,
+                 const U* PhiR, const U* g, U* x, double rtol, int maxit, int* iters, int* state) {
+  const size_t N = (size_t)r0 * n * r1;
+  DArr<U> Ap(ctx, (size_t)a0 * n * n * a1);
+  transpose4_mid<U>(ctx, Ap.p, A, a0, n, n, a1);
+  DArr<float> P;
+  if (precond) {
+    TN_REQUIRE(bj_fits(r0, n, r1), "block-Jacobi preconditioner: blocks too large");
+    DArr<U> work(ctx, bj_work_elems(r0, n, r1, a0, a1));
+    P = DArr<float>(ctx, (size_t)r1 * r0 * n * r0 * n);
+    DArr<int> flag(ctx, 1);
+    TN_REQUIRE(bj_setup<U>(ctx, r0, n, r1, a0, a1, PhiL, Ap.p, PhiR, P.p, work.p, work.n, flag.p),
+               "block-Jacobi preconditioner: a block is not positive definite");
+  }
+  FusedCg f;
+  const FcgPlan pl = f.plan<U>(ctx, r0, n, r1, a0, a1, precond != 0);
+  TN_REQUIRE(pl.ok, "fused conjugate gradients: shape outside the kernel's limits");
+  const double gn = nrm2<U>(ctx, g, N);
+  *iters = f.run<U>(ctx, pl, r0, n, r1, a0, a1, PhiL, Ap.p, PhiR, precond ? P.p : nullptr, g, x,
+                    rtol * rtol * gn * gn, maxit, state);
+}
+
+}  // namespace tnfem
 
 extern "C" {
 
@@ -393,6 +424,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
       p.seed = opts->seed;
       p.precond = opts->no_precond == 0;
       p.local_rtol = opts->local_rtol < 0 ? 1e-2 : opts->local_rtol;
+      p.fused_cg = opts->cg_engine == 0;
       p.local_mixed = opts->precision == TNFEM_MIXED_LOCAL;
       p.verbose = getenv("TNFEM_VERBOSE") != nullptr;
       AmenStats s;
@@ -703,6 +735,25 @@ tnfem_status tnfem_op_local_matvec(tnfem_ctx* ctx, int r0, int n, int r1, int a0
     transpose4_mid<double>(ctx, Ap.p, A, a0, n, n, a1);
     DArr<double> ws(ctx, local_ws_elems(r0, n, r1, a0, a1));
     local_matvec<double>(ctx, r0, n, r1, a0, a1, PhiL, Ap.p, PhiR, x, y, ws.p, ws.n);
+    sync(ctx);
+  });
+}
+
+tnfem_status tnfem_op_local_cg(tnfem_ctx* ctx, int precision, int precond, int r0, int n, int r1, int a0, int a1,
+                               const void* PhiL, const void* A, const void* PhiR, const void* g, void* x,
+                               double rtol, int maxit, int* iters, int* state) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    TN_REQUIRE(PhiL && A && PhiR && g && x && iters && state, "null pointer");
+    TN_REQUIRE(r0 >= 1 && r1 >= 1 && n >= 1 && a0 >= 1 && a1 >= 1, "sizes must be positive");
+    TN_REQUIRE(n <= 8, "mode size above 8");
+    TN_REQUIRE(maxit >= 0 && rtol >= 0.0, "maxit and rtol must be non-negative");
+    if (precision == TNFEM_FP64)
+      tnfem::op_local_cg<double>(ctx, precond, r0, n, r1, a0, a1, (const double*)PhiL, (const double*)A,
+                          (const double*)PhiR, (const double*)g, (double*)x, rtol, maxit, iters, state);
+    else
+      tnfem::op_local_cg<float>(ctx, precond, r0, n, r1, a0, a1, (const float*)PhiL, (const float*)A, (const float*)PhiR,
+                         (const float*)g, (float*)x, rtol, maxit, iters, state);
     sync(ctx);
   });
 }

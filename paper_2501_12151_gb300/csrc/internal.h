@@ -96,6 +96,9 @@ struct ProfScope {
   ProfScope(tnfem_ctx* c, int cls, double flops, double bytes, bool device_timed = false);
   ~ProfScope();
 };
+// Set the algorithmic work of the sampled launch `idx` (ProfScope::idx; ignored when < 0), for
+// launches whose work is known only after they ran.
+void prof_set_work(tnfem_ctx* ctx, int idx, double flops, double bytes);
 
 // Device-side duration of one kernel launch, accumulated over every execution of that launch
 // (including each replay of a graph that captured it): the first CTA to start records the

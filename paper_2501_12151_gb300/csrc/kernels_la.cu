@@ -259,8 +259,10 @@ struct GridBar {
 
 constexpr long long kBarSpin = 1ll << 24;
 
-// true when all CTAs arrived and no CTA reported an error
+// true when all CTAs arrived and no CTA reported an error (thread 0 reads the flag and broadcasts
+// it, so the threads of a CTA cannot disagree)
 __device__ bool grid_barrier(GridBar* bar) {
+  __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &bar->gen;
@@ -280,9 +282,10 @@ __device__ bool grid_barrier(GridBar* bar) {
       }
     }
     __threadfence();
+    s_ok = *((volatile int*)&bar->err) == 0;
   }
   __syncthreads();
-  return *((volatile int*)&bar->err) == 0;
+  return s_ok != 0;
 }
 
 template <typename T>

@@ -93,6 +93,12 @@ ProfScope::ProfScope(tnfem_ctx* c, int cls, double flops, double bytes, bool dev
   idx = (int)ctx->prof_pending.size() - 1;
 }
 
+void prof_set_work(tnfem_ctx* ctx, int idx, double flops, double bytes) {
+  if (idx < 0 || idx >= (int)ctx->prof_pending.size()) return;
+  ctx->prof_pending[idx].flops = flops;
+  ctx->prof_pending[idx].bytes = bytes;
+}
+
 ProfScope::~ProfScope() {
   if (idx < 0) return;
   // a failed record only loses this sample; destructors must not throw

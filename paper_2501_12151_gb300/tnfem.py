@@ -49,7 +49,7 @@ class COpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("rank_cap", C.c_int), ("kickrank", C.c_int), ("max_sweeps", C.c_int),
                 ("precision", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int),
                 ("seed", C.c_uint64), ("local_maxit", C.c_int), ("no_precond", C.c_int),
-                ("tensor_cores", C.c_int), ("local_rtol", C.c_double)]
+                ("tensor_cores", C.c_int), ("local_rtol", C.c_double), ("cg_engine", C.c_int)]
 
 
 class CInfo(C.Structure):
@@ -119,11 +119,13 @@ _sig("tnfem_op_local_matvec_noalloc", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _v
 _ll = C.c_longlong
 _sig("tnfem_op_gemm_f32", _i, [_vp, _i, _i, _i, _i, _i] + [_ll] * 9 + [C.c_float, _vp, _vp, C.c_float, _vp])
 _sig("tnfem_op_local_matvec_f32", _i, [_vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
+_sig("tnfem_op_local_cg", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, C.c_double, _i,
+                               C.POINTER(C.c_int), C.POINTER(C.c_int)])
 _sig("tnfem_measure_fma_peak", _i, [_vp, _i, _pd])
 _sig("tnfem_profile_start", _i, [_vp, _i])
 _sig("tnfem_profile_read", _i, [_vp, _i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pd, _pd, _pd])
 
-PROF_CLASSES = {"contract32": 0, "contract64": 1, "krylov": 2, "qr": 3, "svd": 4, "other": 5}
+PROF_CLASSES = {"contract32": 0, "contract64": 1, "krylov": 2, "qr": 3, "svd": 4, "other": 5, "cg32": 6, "cg64": 7}
 
 
 # ---------------------------------------------------------------------------------------
@@ -192,6 +194,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.no_precond = 0 if getattr(o, "precond", True) else 1
     co.tensor_cores = 1 if getattr(o, "tensor_cores", False) else 0
     co.local_rtol = float(getattr(o, "local_rtol", -1.0))
+    co.cg_engine = 0 if getattr(o, "fused_cg", True) else 1
     return co
 
 
@@ -381,6 +384,14 @@ class Context:
 
     def op_local_matvec_f32(self, engine, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y):
         self.check(lib.tnfem_op_local_matvec_f32(self.h, engine, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y))
+
+    def op_local_cg(self, precision, precond, r0, n, r1, a0, a1, PhiL, A, PhiR, g, x, rtol, maxit):
+        """Fused preconditioned CG on one local system; returns (iterations, state)."""
+        its, st = C.c_int(0), C.c_int(0)
+        prec = 0 if precision in ("fp64", 0) else 1
+        self.check(lib.tnfem_op_local_cg(self.h, prec, int(precond), r0, n, r1, a0, a1, PhiL, A, PhiR, g, x, float(rtol), int(maxit),
+                                         C.byref(its), C.byref(st)))
+        return its.value, st.value
 
     def op_qr(self, m, n, A, Q, R):
         self.check(lib.tnfem_op_qr(self.h, m, n, A, Q, R))

@@ -90,6 +90,7 @@ class SolveOpts:
     precond: bool = True      # block-Jacobi preconditioned local solves
     tensor_cores: bool = False  # binary32 contractions on the tcgen05 tensor cores
     local_rtol: float = -1.0    # local solves to this fraction of their starting residual (<0: default)
+    fused_cg: bool = True       # local CG as one persistent kernel (False: a launch per step)
 
 
 @dataclass
