@@ -114,7 +114,7 @@ struct FcgArgs {
   U* ws;          // packed operators and the iteration's vectors (fcg_dims layout)
   double* parts;  // pap [n2], rr [2][n3], rz [2][n3]
   int* ctl;       // [0] state, [1] iterations; FcgBar at ctl + 4; group counters from ctl + 64
-  unsigned long long* tprof;  // nullable: SM cycles per phase summed over CTAs and passes (7 slots)
+  unsigned long long* tprof;  // nullable: SM cycles per phase summed over CTAs (7 slots), then passes
 };
 
 // true when every CTA arrived and none reported an error (one answer for the whole CTA: thread 0
@@ -185,10 +185,21 @@ __device__ __forceinline__ V warp_allsum(V v) {
   return v;
 }
 
-// Sum of part[0..cnt) in a fixed order, formed by the calling warp and returned to all its lanes.
+// Sum of part[0..cnt) in a fixed order, formed by the calling warp and returned to all its lanes;
+// each lane requests up to 16 of its values at once (one round trip for up to 512 partials).
 __device__ __forceinline__ double warp0_sum(const double* part, int cnt) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int i = threadIdx.x & 31; i < cnt; i += 32) s += __ldcg(part + i);
+  for (int base = 0; base < cnt; base += 512) {
+    double v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int i = base + lane + 32 * j;
+      v[j] = i < cnt ? __ldcg(part + i) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s += v[j];
+  }
   return warp_allsum(s);
 }
 
@@ -240,16 +251,25 @@ __device__ __forceinline__ void cpa_wait() {
 }
 
 // rows x w4 elements (w4 a multiple of 4) from src (row stride lds) to dst (row stride ldd), in
-// 16-byte pieces; every row start 16-byte aligned on both sides
+// 16-byte pieces; every row start 16-byte aligned on both sides.  Thread t copies piece t % per of
+// rows t / per, t / per + FT / per, ... (per = pieces of a row; one division per call).
 template <typename U>
 __device__ __forceinline__ void copy_rows(U* dst, int ldd, const U* src, size_t lds, int rows, int w4) {
   constexpr int E = 16 / sizeof(U);  // elements per piece
   const int per = w4 / E;
-  const int total = rows * per;
-  for (int e = threadIdx.x; e < total; e += FT) {
-    const int r = e / per, c = (e - r * per) * E;
-    cp16(dst + (size_t)r * ldd + c, src + (size_t)r * lds + c);
+  if (per <= 0) return;
+  if (per > FT) {
+    for (int e = threadIdx.x; e < rows * per; e += FT) {
+      const int r = e / per, c = (e - r * per) * E;
+      cp16(dst + (size_t)r * ldd + c, src + (size_t)r * lds + c);
+    }
+    return;
   }
+  const int rstep = FT / per;
+  const int r0 = threadIdx.x / per;
+  if (r0 >= rstep) return;
+  const int c = (threadIdx.x - r0 * per) * E;
+  for (int r = r0; r < rows; r += rstep) cp16(dst + (size_t)r * ldd + c, src + (size_t)r * lds + c);
 }
 // cnt elements (a multiple of 16 bytes) from src to dst, both 16-byte aligned
 template <typename U>
@@ -285,20 +305,26 @@ __device__ __forceinline__ Mk mk_setup(int rows, int cols) {
   return k;
 }
 
-// acc += sum over the k of [0, kc) that belong to the thread's group (every k with one group)
-template <typename U>
-__device__ __forceinline__ void tile_fma(const U* as, const U* bs, int kc, const Mk& mk, U (&acc)[4][4]) {
-  const int step = mk.ngrp;
+// acc += sum over the k of [0, kc) that belong to the thread's group (NG groups take alternate k)
+template <typename U, int NG>
+__device__ __forceinline__ void tile_fma_g(const U* as, const U* bs, int kc, const Mk& mk, U (&acc)[4][4]) {
+  const U* pa = as + 4 * mk.ty + mk.grp * kTL;
+  const U* pb = bs + 4 * mk.tx + mk.grp * kTL;
 #pragma unroll 4
-  for (int kk = mk.grp; kk < kc; kk += step) {
+  for (int kk = mk.grp; kk < kc; kk += NG, pa += NG * kTL, pb += NG * kTL) {
     U a[4], b[4];
-    ld4(as + kk * kTL + 4 * mk.ty, a);
-    ld4(bs + kk * kTL + 4 * mk.tx, b);
+    ld4(pa, a);
+    ld4(pb, b);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fmaU(a[i], b[j], acc[i][j]);
   }
+}
+template <typename U>
+__device__ __forceinline__ void tile_fma(const U* as, const U* bs, int kc, const Mk& mk, U (&acc)[4][4]) {
+  if (mk.ngrp == 2) tile_fma_g<U, 2>(as, bs, kc, mk, acc);
+  else tile_fma_g<U, 1>(as, bs, kc, mk, acc);
 }
 
 // Sum the second group's accumulators into the first's through red (>= 64 x 64 elements, free).
@@ -318,6 +344,52 @@ __device__ __forceinline__ void tile_reduce(const Mk& mk, U (&acc)[4][4], U* red
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] += red[(4 * mk.ty + i) * 64 + 4 * mk.tx + j];
+  }
+}
+
+// Phase 2, second contraction on one staged chunk of PhiR rows: for the chunk's nb rows b',
+// out[i][b'] = sum_{k<K3} T2s[i][k] buf[b'][k] (i < NN), two b' per warp with the lanes along k;
+// lane 0 stores the shares and accumulates p.Bp (PN = row a' of p, unused in the first pass).
+template <typename U, int NN>
+__device__ __forceinline__ void stage3(const U* T2s, const U* buf, int K3, int K3p, int nb, int b0, int r1,
+                                       U* Ybase, int mp, const U* PN, bool first, double& pap) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int bl = 2 * warp; bl < nb; bl += 2 * (FT / 32)) {
+    const bool two = bl + 1 < nb;
+    const U* p0 = buf + (size_t)bl * K3p;
+    const U* p1 = two ? p0 + K3p : p0;
+    U s0[NN], s1[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      s0[i] = U(0);
+      s1[i] = U(0);
+    }
+    for (int k = lane; k < K3; k += 32) {
+      const U w0 = p0[k], w1 = p1[k];
+#pragma unroll
+      for (int i = 0; i < NN; ++i) {
+        const U t = T2s[i * K3 + k];
+        s0[i] = fmaU(t, w0, s0[i]);
+        s1[i] = fmaU(t, w1, s1[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      s0[i] = warp_allsum(s0[i]);
+      s1[i] = warp_allsum(s1[i]);
+    }
+    if (lane == 0) {
+      const int bpp = b0 + bl;
+#pragma unroll
+      for (int i = 0; i < NN; ++i) {
+        Ybase[(size_t)bpp * mp + i] = s0[i];
+        if (!first) pap += (double)PN[i * r1 + bpp] * (double)s0[i];
+        if (two) {
+          Ybase[(size_t)(bpp + 1) * mp + i] = s1[i];
+          if (!first) pap += (double)PN[i * r1 + bpp + 1] * (double)s1[i];
+        }
+      }
+    }
   }
 }
 
@@ -407,7 +479,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
   // optional phase timing (thread 0 of every CTA): work and barrier wait of each phase
   const bool tp = A.tprof != nullptr && threadIdx.x == 0;
   long long tmark = tp ? clock64() : 0;
-  long long tacc[6] = {0, 0, 0, 0, 0, 0};
+  long long tacc[7] = {0, 0, 0, 0, 0, 0, 0};
   auto mark = [&](int slot) {
     if (tp) {
       const long long t = clock64();
@@ -446,10 +518,10 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
           __syncthreads();
           copy_rows<U>(as, kTL, PLt + (size_t)k0 * D.M1p + row0, D.M1p, kc, rows4);
           if (first) {
-            for (int e = threadIdx.x; e < kc * cols4; e += FT) {
-              const int kb = e / cols4, cc = e - kb * cols4;
+            const int cc = threadIdx.x & 63;
+            for (int kb = threadIdx.x >> 6; kb < kc; kb += FT / 64) {
               if (cc < cols) cp1(bz + kb * kTL + cc, A.x + (size_t)(k0 + kb) * N1 + col0 + cc);
-              else bz[kb * kTL + cc] = U(0);
+              else if (cc < cols4) bz[kb * kTL + cc] = U(0);
             }
           } else {
             copy_rows<U>(bz, kTL, Z + (size_t)k0 * D.N1p + col0, D.N1p, kc, cols4);
@@ -459,11 +531,13 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
           cpa_wait<0>();
           __syncthreads();
           if (!first) {
-            for (int e = threadIdx.x; e < kc * cols; e += FT) {
-              const int kb = e / cols, cc = e - kb * cols;
-              const U v = pass == 1 ? bz[kb * kTL + cc] : fmaU(beta, bp[kb * kTL + cc], bz[kb * kTL + cc]);
-              bz[kb * kTL + cc] = v;
-              if (own) pnew[(size_t)(k0 + kb) * D.N1p + col0 + cc] = v;
+            const int cc = threadIdx.x & 63;
+            if (cc < cols) {
+              for (int kb = threadIdx.x >> 6; kb < kc; kb += FT / 64) {
+                const U v = pass == 1 ? bz[kb * kTL + cc] : fmaU(beta, bp[kb * kTL + cc], bz[kb * kTL + cc]);
+                bz[kb * kTL + cc] = v;
+                if (own) pnew[(size_t)(k0 + kb) * D.N1p + col0 + cc] = v;
+              }
             }
             __syncthreads();
           }
@@ -508,7 +582,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
         // PhiR chunk are requested now and arrive while T2 is formed
         const int K3 = gc * r1;
         int nbc = max(1, min(r1, PRB / D.K3p));
-        if (nbc > FT / 32 && nbc < r1) nbc -= nbc % (FT / 32);  // whole rounds of the warps
+        if (nbc > FT / 16 && nbc < r1) nbc -= nbc % (FT / 16);  // whole rounds of the warps (2 b' each)
         const int nchk = (r1 + nbc - 1) / nbc;
         const U* PRslice = PRk + (size_t)gs * r1 * D.K3p;
         auto issue3 = [&](int c) {
@@ -559,6 +633,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
           }
           __syncthreads();  // the reduction buffer is the next tile's chunk buffer
         }
+        mark(2);  // (timing only: the items' two contractions are accumulated in separate slots)
         // (B p)[a'][i][b'] share: sum over k = (g - g0, b) of T2s[i][k] PhiR[b'][g0 + .][.], with
         // the slice's PhiR rows staged nbc b' at a time (chunk 0 requested at the item's start)
         double pap = 0.0, unused = 0.0;
@@ -572,30 +647,16 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
           __syncthreads();  // T2s complete (first chunk) and this chunk's PhiR staged
           const U* buf = PRs + (c & 1) * PRB;
           const int b0 = c * nbc, nb = min(nbc, r1 - b0);
-          for (int bl = warp; bl < nb; bl += FT / 32) {
-            U sacc[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sacc[i] = U(0);
-            const U* prp = buf + (size_t)bl * D.K3p;
-            for (int k = lane; k < K3; k += 32) {
-              const U w = prp[k];
-#pragma unroll
-              for (int i = 0; i < 8; ++i)
-                if (i < n) sacc[i] = fmaU(T2s[i * K3 + k], w, sacc[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (i < n) sacc[i] = warp_allsum(sacc[i]);
-            if (lane == 0) {
-              const int bpp = b0 + bl;
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                if (i < n) {
-                  Y[((size_t)gs * r1 + bpp) * mp + ap * n + i] = sacc[i];
-                  if (!first) pap += (double)PN[i * r1 + bpp] * (double)sacc[i];
-                }
-              }
-            }
+          U* Ybase = Y + (size_t)gs * r1 * mp + ap * n;
+          switch (n) {
+            case 1: stage3<U, 1>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            case 2: stage3<U, 2>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            case 3: stage3<U, 3>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            case 4: stage3<U, 4>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            case 5: stage3<U, 5>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            case 6: stage3<U, 6>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            case 7: stage3<U, 7>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
+            default: stage3<U, 8>(T2s, buf, K3, D.K3p, nb, b0, r1, Ybase, mp, PN, first, pap); break;
           }
           __syncthreads();  // the buffer is refilled two chunks later
         }
@@ -603,9 +664,9 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
         if (threadIdx.x == 0) ppap[item] = pap;
       }
     }
-    mark(2);
-    if (!fcg_sync(A.ctl)) return;
     mark(3);
+    if (!fcg_sync(A.ctl)) return;
+    mark(4);
 
     // ---- phase 3: alpha; r -= alpha B p; z = M^{-1} r; x += alpha p; r.r and r.z shares -------------
     U alpha = U(0);
@@ -727,7 +788,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
       }
     }
     if (!first) ++it;
-    mark(4);
+    mark(5);
     if (!fcg_sync(A.ctl)) return;
 
     // ---- stop test and beta of the next pass -----------------------------------------------
@@ -746,7 +807,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
       s_sc[1] = first ? 0.0 : rzn / rzo;
     }
     __syncthreads();
-    mark(5);
+    mark(6);
     if (s_state) {
       state = s_state == 1 ? 1 : 0;
       break;
@@ -754,8 +815,8 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
     beta = (U)s_sc[1];
   }
   if (tp) {
-    for (int i = 0; i < 6; ++i) atomicAdd(A.tprof + i, (unsigned long long)tacc[i]);
-    atomicAdd(A.tprof + 6, (unsigned long long)passes);
+    for (int i = 0; i < 7; ++i) atomicAdd(A.tprof + i, (unsigned long long)tacc[i]);
+    atomicAdd(A.tprof + 7, (unsigned long long)passes);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     A.ctl[0] = state;
@@ -773,9 +834,10 @@ int sm_count(tnfem_ctx* ctx) {
 
 FusedCg::~FusedCg() {
   if (prof_on_ && prof_passes_ > 0) {
-    static const char* names[6] = {"phase 1", "barrier 1", "phase 2", "barrier 2", "phase 3", "barrier 3"};
+    static const char* names[7] = {"phase 1",   "barrier 1", "phase 2 T2", "phase 2 Bp",
+                                   "barrier 2", "phase 3",   "barrier 3"};
     fprintf(stderr, "[tnfem] fused CG: %.0f passes; SM cycles per pass (mean over CTAs):", prof_passes_);
-    for (int i = 0; i < 6; ++i) fprintf(stderr, " %s %.0f", names[i], prof_cycles_[i] / prof_passes_);
+    for (int i = 0; i < 7; ++i) fprintf(stderr, " %s %.0f", names[i], prof_cycles_[i] / prof_passes_);
     fprintf(stderr, "\n");
   }
   if (ctx_) {
@@ -936,8 +998,8 @@ int FusedCg::run(tnfem_ctx* ctx, const FcgPlan& pl, int r0, int n, int r1, int a
   if (prof_on_) {
     unsigned long long h[8];
     TN_CHECK_CUDA(cudaMemcpy(h, tprof_, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < 6; ++i) prof_cycles_[i] += (double)h[i] / std::max(1, pl.ncta);
-    prof_passes_ += (double)h[6] / std::max(1, pl.ncta);
+    for (int i = 0; i < 7; ++i) prof_cycles_[i] += (double)h[i] / std::max(1, pl.ncta);
+    prof_passes_ += (double)h[7] / std::max(1, pl.ncta);
   }
   // algorithmic work: its + 1 local matvecs and block-Jacobi applies
   const double mm = (double)r0 * n;

@@ -54,7 +54,7 @@ class FusedCg {
   // TNFEM_FCG_PROF set: SM cycles per phase of every launch, summed and reported at destruction
   bool prof_on_ = false;
   unsigned long long* tprof_ = nullptr;
-  double prof_cycles_[6] = {};
+  double prof_cycles_[7] = {};
   double prof_passes_ = 0.0;
 };
 

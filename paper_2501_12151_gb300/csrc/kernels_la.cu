@@ -4,6 +4,8 @@
 // memory (L2/L1-resident at these sizes); all loops have fixed trip counts, nothing waits on
 // another block.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cfloat>
 
 #include "internal.h"
@@ -405,6 +407,31 @@ void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
   check_launch(ctx, "qr");
 }
 
+// TNFEM_SVD_PROF set: Jacobi sweeps of every cooperative SVD, reported at process exit.
+struct SvdStats {
+  bool on = getenv("TNFEM_SVD_PROF") != nullptr;
+  long long calls = 0, sweeps = 0, mn = 0;
+  int hist[16] = {};
+  void add(int m, int n, int sw) {
+    ++calls;
+    sweeps += sw;
+    mn += (long long)m * n;
+    ++hist[std::min(sw, 15)];
+  }
+  ~SvdStats() {
+    if (!on || calls == 0) return;
+    fprintf(stderr, "[tnfem] cooperative SVD: %lld calls, %.2f sweeps per call (incl. the checking sweep), mean m*n %.0f; sweeps histogram:",
+            calls, (double)sweeps / calls, (double)mn / calls);
+    for (int i = 0; i < 16; ++i)
+      if (hist[i]) fprintf(stderr, " %d:%d", i, hist[i]);
+    fprintf(stderr, "\n");
+  }
+};
+SvdStats& svd_stats() {
+  static SvdStats st;
+  return st;
+}
+
 template <typename T>
 void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   if (m <= 0 || n <= 0) return;
@@ -433,6 +460,14 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
     TN_CHECK_CUDA(cudaMemcpyAsync(&err, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     sync(ctx);
     if (err) throw Error(TNFEM_E_TIMEOUT, "svd: a grid barrier wait expired");
+    if (svd_stats().on) {
+      // sweeps done = index of the first sweep without a rotation, plus that checking sweep
+      int rot[127];
+      TN_CHECK_CUDA(cudaMemcpy(rot, bar->rot, sizeof(rot), cudaMemcpyDeviceToHost));
+      int sw = 0;
+      while (sw < max_sweeps && sw < 127 && rot[sw] != 0) ++sw;
+      svd_stats().add(m, n, std::min(sw + 1, max_sweeps));
+    }
     return;
   }
   ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
