@@ -338,6 +338,15 @@ tnfem_status tnfem_op_local_matvec_f32(tnfem_ctx* ctx, int engine, int r0, int n
 /* Reduced Householder QR of an m x n row-major matrix: Q [m][k], R [k][n], k = min(m, n),
  * diag(R) >= 0 is not enforced (Householder signs). */
 tnfem_status tnfem_op_qr(tnfem_ctx* ctx, int m, int n, const double* Ain, double* Q, double* R);
+/* a7 (enrichment): Q, R of the m x (rk + w) row-major A = [U | W] whose first rk columns are
+ * orthonormal (the left singular vectors of the truncation).  W is orthogonalised against U by
+ * block Gram-Schmidt (twice) and its remainder by Householder QR, so A = [U | Q_w] [[I, C], [0,
+ * R_w]]: Q [m][rk + w] has orthonormal columns, R [rk + w][rk + w] is upper triangular with
+ * R[:, :rk] = [I; 0].  When W lies numerically inside span(U) the Householder QR of the whole
+ * (projected) A is taken instead (Q R = A still holds; R[:, :rk] = Q^T U).  Requires m >= rk + w; A is
+ * overwritten; binary64 device pointers.  Not a separate step of the paper: the same QR as
+ * tnfem_op_qr of the enriched basis, exploiting U's orthonormality. */
+tnfem_status tnfem_op_qr_ext(tnfem_ctx* ctx, int m, int rk, int w, double* A, double* Q, double* R);
 /* Thin SVD by one-sided Jacobi of an m x n row-major matrix (m >= n): U [m][n] with unit
  * columns, S [n] descending, Vt [n][n].  Each column pair of U is signed so that its entry of
  * largest magnitude is positive. */

@@ -1088,7 +1088,8 @@ void Amen<T>::core_step(int k, AmenStats& st) {
     // enrichment block into Ue's last rz1 columns, then QR
     pack_cols_kernel<T><<<nblk((long long)m * rz1), RT, 0, ctx_->stream>>>(Ue_.p, crs_.p, m, rz1, rz1, ue_cols, rk);
     count_launch(ctx_);
-    qr<T>(ctx_, m, ue_cols, Ue_.p, Q_.p, R_.p, qrw_.p);
+    // U_rk has orthonormal columns: only the rz1 enrichment columns need orthogonalising
+    qr_ext<T>(ctx_, m, rk, rz1, Ue_.p, Q_.p, R_.p, qrw_.p, qrw_.n);
     kq = std::min(m, ue_cols);
     // Vnew = R[:, :rk] V   (kq x r1)
     GemmDesc gv{kq, r1, rk, 1, ue_cols, 1, 0, r1, 1, 0, r1, 1, 0};

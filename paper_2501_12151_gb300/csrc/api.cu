@@ -828,6 +828,17 @@ tnfem_status tnfem_op_qr(tnfem_ctx* ctx, int m, int n, const double* Ain, double
   });
 }
 
+tnfem_status tnfem_op_qr_ext(tnfem_ctx* ctx, int m, int rk, int w, double* A, double* Q, double* R) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    TN_REQUIRE(A && Q && R, "null pointer");
+    TN_REQUIRE(rk >= 1 && w >= 1 && m >= rk + w, "needs rk >= 1, w >= 1 and m >= rk + w");
+    DArr<double> work(ctx, qr_ext_work_elems(m, rk, w) + qr_work_elems(m, rk + w));
+    qr_ext<double>(ctx, m, rk, w, A, Q, R, work.p, work.n);
+    sync(ctx);
+  });
+}
+
 tnfem_status tnfem_op_svd(tnfem_ctx* ctx, int m, int n, const double* Ain, double* U, double* S, double* Vt) {
   if (!ctx) return TNFEM_E_INVALID;
   return guard(ctx, [&] {

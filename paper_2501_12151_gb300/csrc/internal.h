@@ -211,6 +211,14 @@ template <typename T> void transpose2(tnfem_ctx* ctx, T* out, const T* in, int m
 template <typename T>
 void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work);
 size_t qr_work_elems(int m, int n);
+// QR of the m x (rk + w) row-major A = [U | W] whose first rk columns are orthonormal (m >= rk + w):
+// Q [m][rk + w], R [rk + w][rk + w] as qr() gives them, up to the basis of the W part (block
+// Gram-Schmidt against U, with a Householder fallback when W lies inside span(U)); A is
+// overwritten.  work holds qr_ext_work_elems(m, rk, w) elements; with less, or w < 1, or rk < 1,
+// this is qr().  Synchronises the stream.
+size_t qr_ext_work_elems(int m, int rk, int w);
+template <typename T>
+void qr_ext(tnfem_ctx* ctx, int m, int rk, int w, T* A, T* Q, T* R, T* work, size_t work_elems);
 // Thin SVD by one-sided Jacobi of row-major m x n matrix (m >= n), A overwritten:
 // U [m][n] (unit columns, sign fixed), S [n] descending, Vt [n][n].
 template <typename T>

@@ -46,9 +46,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // A: m x n row-major, overwritten by the Householder vectors (below the diagonal) and R.
 // tau: k scalars.  Q: m x k row-major (explicit), R: k x n row-major.
+// The whole CTA (any multiple of 32 threads) takes part.
 template <typename T>
-__global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A, T* __restrict__ Q,
-                                                T* __restrict__ R, T* __restrict__ tau) {
+__device__ void qr_body(int m, int n, T* __restrict__ A, T* __restrict__ Q, T* __restrict__ R, T* __restrict__ tau) {
   __shared__ T sh[33];
   __shared__ T s_beta, s_tau, s_v0;
   const int k = min(m, n);
@@ -130,6 +130,40 @@ __global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A,
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A, T* __restrict__ Q,
+                                                T* __restrict__ R, T* __restrict__ tau) {
+  qr_body(m, n, A, Q, R, tau);
+}
+
+// Jacobi rotation (cs, sn) annihilating the off-diagonal c of the column-pair Gram block
+// [[a, c], [c, b]]: t = tan(theta) is the smaller root of c t^2 + (b - a) t - c = 0,
+// t = 2c / (d + sign(d) sqrt(d^2 + 4c^2)) with d = b - a, evaluated in binary32 on power-of-two
+// scaled d and c (binary64 division and square root are long sequences on this part); cs and sn
+// are then formed in binary64 from t, so the rotation is orthogonal to binary64 rounding whatever
+// the accuracy of t, and an inexact angle only leaves a residual c' ~ 1e-7 c for the next sweep.
+// A t that vanished in binary32 falls back to the binary64 formula.
+__device__ __forceinline__ void jacobi_rotation(double a, double b, double c, double& cs, double& sn) {
+  const double d = b - a;
+  int e = 0;
+  frexp(fmax(fabs(d), fabs(c)), &e);
+  const float d32 = (float)ldexp(d, -e), c32 = (float)ldexp(c, -e);
+  const float r = sqrtf(d32 * d32 + 4.0f * c32 * c32);
+  double t = (double)(2.0f * c32 / (d32 >= 0.0f ? d32 + r : d32 - r));
+  if (!(t != 0.0) || !isfinite(t)) {
+    const double zeta = d / (2.0 * c);
+    t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  }
+  cs = rsqrt(1.0 + t * t);
+  sn = cs * t;
+}
+__device__ __forceinline__ void jacobi_rotation(float a, float b, float c, float& cs, float& sn) {
+  const float zeta = (b - a) / (2.0f * c);
+  const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+  cs = rsqrtf(1.0f + t * t);
+  sn = cs * t;
+}
+
 // One-sided Jacobi SVD.  G: m x n column-major work copy of A, V: n x n column-major.
 // With use_smem the working copies G, V and sig live in dynamic shared memory (when they fit);
 // otherwise in the global work buffers passed in.
@@ -173,16 +207,14 @@ __global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restri
         }
         a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
         if (c == T(0) || a == T(0) || b == T(0)) continue;
-        // the rotation is computed by one lane and broadcast: square roots and divisions are long
-        // FMA sequences, and binary64 FMA throughput is scarce on this part
+        // the rotation is computed by one lane and broadcast (see jacobi_rotation: binary64
+        // square roots and divisions are long sequences, and binary64 throughput is scarce)
         T cs = T(1), sn = T(0);
         int rotate = 0;
-        if (lane == 0 && fabs(c) > tol * sqrt(a * b)) {
-          const T zeta = (b - a) / (T(2) * c);
-          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          cs = T(1) / sqrt(T(1) + t * t);
-          sn = cs * t;
-          rotate = 1;
+        if (lane == 0) {
+          const T tiny = sizeof(T) == 8 ? T(1e-140) : T(1e-17);
+          rotate = (a > tiny && b > tiny) ? (c * c > tol * tol * a * b) : (fabs(c) > tol * sqrt(a * b));
+          if (rotate) jacobi_rotation(a, b, c, cs, sn);
         }
         rotate = __shfl_sync(0xffffffffu, rotate, 0);
         if (!rotate) continue;
@@ -246,7 +278,7 @@ __global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restri
 }
 
 // ---- multi-CTA one-sided Jacobi --------------------------------------------------------------
-// The same rotations as svd_kernel, but each pair of a round is handled by its own CTA (one warp),
+// The same rotations as svd_kernel, but each pair of a round is handled by its own CTA (four warps),
 // so the binary64 work of a round is spread over as many SMs as there are pairs; rounds are
 // separated by a grid barrier.  The kernel is launched cooperatively (all CTAs resident), and
 // every barrier wait is bounded: on expiry the CTA sets err[0], and every CTA leaves at the next
@@ -290,24 +322,34 @@ __device__ bool grid_barrier(GridBar* bar) {
   return s_ok != 0;
 }
 
+constexpr int CT = 128;  // threads per CTA of the cooperative SVD: four warps, all four SM partitions
+
+// One-sided Jacobi, one column pair per CTA and round (round-robin ordering), rounds separated by
+// grid barriers.  The four warps of a CTA split the column loops; the pair's three sums meet in
+// shared memory, thread 0 decides the rotation.  Rotate when |c| > tol sqrt(a b), tested as
+// c^2 > tol^2 a b (no square root) unless a or b is so small that the squares could underflow.
 template <typename T>
-__global__ void __launch_bounds__(32) svd_coop_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
+__global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
                                                       T* __restrict__ S, T* __restrict__ Vt, T* G, T* V, T* sig,
                                                       int max_sweeps, GridBar* bar) {
-  const int lane = threadIdx.x;
+  __shared__ T red[3][CT / 32];
+  __shared__ T s_cs, s_sn;
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, ncta = gridDim.x;
   // copy-in: G column-major, V = I (rows spread over CTAs)
-  for (long long t = (long long)cta * 32 + lane; t < (long long)m * n; t += (long long)ncta * 32) {
+  for (long long t = (long long)cta * CT + tid; t < (long long)m * n; t += (long long)ncta * CT) {
     const int i = (int)(t / n), j = (int)(t % n);
     G[(long long)j * m + i] = A[t];
   }
-  for (long long t = (long long)cta * 32 + lane; t < (long long)n * n; t += (long long)ncta * 32) {
+  for (long long t = (long long)cta * CT + tid; t < (long long)n * n; t += (long long)ncta * CT) {
     const int i = (int)(t % n), j = (int)(t / n);
     V[t] = (i == j) ? T(1) : T(0);
   }
   if (!grid_barrier(bar)) return;
   const int np = n + (n & 1);
   const T tol = eps_of<T>() * (T)4;
+  const T tiny = sizeof(T) == 8 ? T(1e-140) : T(1e-17);
   const int sweeps = min(max_sweeps, 127);
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     for (int r = 0; r < np - 1; ++r) {
@@ -320,52 +362,68 @@ __global__ void __launch_bounds__(32) svd_coop_kernel(int m, int n, const T* __r
         T* gp = G + (long long)p * m;
         T* gq = G + (long long)q * m;
         T a = T(0), b = T(0), c = T(0);
-        for (int i = lane; i < m; i += 32) {
+        for (int i = tid; i < m; i += CT) {
           T x = gp[i], y = gq[i];
           a += x * x; b += y * y; c += x * y;
         }
         a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
-        if (c == T(0) || a == T(0) || b == T(0)) continue;
-        T cs = T(1), sn = T(0);
-        int rotate = 0;
-        if (lane == 0 && fabs(c) > tol * sqrt(a * b)) {
-          const T zeta = (b - a) / (T(2) * c);
-          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          cs = T(1) / sqrt(T(1) + t * t);
-          sn = cs * t;
-          rotate = 1;
+        if (lane == 0) {
+          red[0][warp] = a;
+          red[1][warp] = b;
+          red[2][warp] = c;
         }
-        rotate = __shfl_sync(0xffffffffu, rotate, 0);
-        if (!rotate) continue;
-        cs = __shfl_sync(0xffffffffu, cs, 0);
-        sn = __shfl_sync(0xffffffffu, sn, 0);
-        for (int i = lane; i < m; i += 32) {
+        __syncthreads();
+        if (tid == 0) {
+          a = b = c = T(0);
+          for (int w = 0; w < CT / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            c += red[2][w];
+          }
+          int rotate = 0;
+          if (c != T(0) && a != T(0) && b != T(0)) {
+            rotate = (a > tiny && b > tiny) ? (c * c > tol * tol * a * b) : (fabs(c) > tol * sqrt(a * b));
+          }
+          if (rotate) {
+            T cs, sn;
+            jacobi_rotation(a, b, c, cs, sn);
+            s_cs = cs;
+            s_sn = sn;
+            atomicAdd(&bar->rot[sweep], 1);
+          }
+          s_rot = rotate;
+        }
+        __syncthreads();
+        if (!s_rot) continue;
+        const T cs = s_cs, sn = s_sn;
+        for (int i = tid; i < m; i += CT) {
           T x = gp[i], y = gq[i];
           gp[i] = cs * x - sn * y;
           gq[i] = sn * x + cs * y;
         }
         T* vp = V + (long long)p * n;
         T* vq = V + (long long)q * n;
-        for (int i = lane; i < n; i += 32) {
+        for (int i = tid; i < n; i += CT) {
           T x = vp[i], y = vq[i];
           vp[i] = cs * x - sn * y;
           vq[i] = sn * x + cs * y;
         }
-        if (lane == 0) atomicAdd(&bar->rot[sweep], 1);
       }
       if (!grid_barrier(bar)) return;
     }
     if (*((volatile int*)&bar->rot[sweep]) == 0) break;
   }
-  // singular values, then (after a barrier) ranks, signs and outputs; columns spread over CTAs
-  for (int j = cta; j < n; j += ncta) {
+  // singular values, then (after a barrier) ranks, signs and outputs; columns spread over the
+  // warps of all CTAs
+  const int gw = cta * (CT / 32) + warp, nwarp = ncta * (CT / 32);
+  for (int j = gw; j < n; j += nwarp) {
     T s = T(0);
     for (int i = lane; i < m; i += 32) s += G[(long long)j * m + i] * G[(long long)j * m + i];
     s = warp_sum(s);
     if (lane == 0) sig[j] = sqrt(s);
   }
   if (!grid_barrier(bar)) return;
-  for (int j = cta; j < n; j += ncta) {
+  for (int j = gw; j < n; j += nwarp) {
     const T sj = sig[j];
     int pos = 0;
     for (int i = lane; i < n; i += 32) {
@@ -392,6 +450,96 @@ __global__ void __launch_bounds__(32) svd_coop_kernel(int m, int n, const T* __r
   }
 }
 
+// ---- QR of [U | W] with U orthonormal ---------------------------------------------------------
+// Q, R of the m x (rk + w) matrix A = [U | W] (row-major, leading dimension rk + w) when its first
+// rk columns are orthonormal (the left singular vectors of the sweep's truncation, step a7): W is
+// orthogonalised against U by block Gram-Schmidt, twice, W = U C + W''; W'' = Q_w R_w by
+// Householder QR (one CTA); then A = [U | Q_w] [[I, C], [0, R_w]], the same factorisation as the
+// Householder QR of A up to the basis of the W part.  When W'' lies numerically inside span(U)
+// the QR of W'' completes it with directions that need not be orthogonal to U; that is detected
+// (max |U^T Q_w| > 1e-10) and CTA 0 then takes the Householder QR of the projected (same-span)
+// A' = Q R' instead, with R corrected so that Q R = A still holds.  One cooperative launch, grid
+// barriers between the phases, every wait bounded.
+template <typename T>
+__global__ void __launch_bounds__(CT) qr_ext_coop_kernel(int m, int rk, int w, T* __restrict__ A, T* __restrict__ Q,
+                                                         T* __restrict__ R, T* __restrict__ work, GridBar* bar) {
+  const int ld = rk + w;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gwarp = blockIdx.x * (CT / 32) + (tid >> 5), nwarp = gridDim.x * (CT / 32);
+  const int gthr = blockIdx.x * CT + tid, nthr = gridDim.x * CT;
+  T* Cp = work;                    // [rk][w] this pass's coefficients
+  T* Ca = Cp + (size_t)rk * w;     // [rk][w] accumulated coefficients
+  T* Wc = Ca + (size_t)rk * w;     // [m][w] remainder, contiguous
+  T* Qw = Wc + (size_t)m * w;      // [m][w]
+  T* Rw = Qw + (size_t)m * w;      // [w][w]
+  T* tau = Rw + (size_t)w * w;     // [max(w, ld)]
+  T* emax = tau + ld;              // [nwarp]
+  const T* U = A;
+  T* W = A + rk;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int it = gwarp; it < rk * w; it += nwarp) {
+      const int k = it / w, j = it - k * w;
+      T sacc = T(0);
+      for (int i = lane; i < m; i += 32) sacc += U[(size_t)i * ld + k] * W[(size_t)i * ld + j];
+      sacc = warp_sum(sacc);
+      if (lane == 0) {
+        Cp[it] = sacc;
+        Ca[it] = pass == 0 ? sacc : Ca[it] + sacc;
+      }
+    }
+    if (!grid_barrier(bar)) return;
+    for (int t = gthr; t < m * w; t += nthr) {
+      const int i = t / w, j = t - i * w;
+      T sacc = T(0);
+      for (int k = 0; k < rk; ++k) sacc += U[(size_t)i * ld + k] * Cp[k * w + j];
+      W[(size_t)i * ld + j] -= sacc;
+    }
+    if (!grid_barrier(bar)) return;
+  }
+  if (blockIdx.x == 0) {
+    for (int t = tid; t < m * w; t += CT) Wc[t] = W[(size_t)(t / w) * ld + t % w];
+    __syncthreads();
+    qr_body(m, w, Wc, Qw, Rw, tau);
+  }
+  if (!grid_barrier(bar)) return;
+  // orthogonality of Q_w to U
+  T mx = T(0);
+  for (int it = gwarp; it < rk * w; it += nwarp) {
+    const int k = it / w, j = it - k * w;
+    T sacc = T(0);
+    for (int i = lane; i < m; i += 32) sacc += U[(size_t)i * ld + k] * Qw[(size_t)i * w + j];
+    mx = fmax(mx, fabs(warp_sum(sacc)));
+  }
+  if (lane == 0) emax[gwarp] = mx;
+  if (!grid_barrier(bar)) return;
+  T worst = T(0);
+  for (int i = 0; i < nwarp; ++i) worst = fmax(worst, emax[i]);
+  if (worst <= T(1e-10)) {
+    // Q = [U | Q_w], R = [[I, C], [0, R_w]]
+    for (int t = gthr; t < m * ld; t += nthr) {
+      const int i = t / ld, c = t - i * ld;
+      Q[t] = c < rk ? U[(size_t)i * ld + c] : Qw[(size_t)i * w + (c - rk)];
+    }
+    for (int t = gthr; t < ld * ld; t += nthr) {
+      const int i = t / ld, c = t - i * ld;
+      T v;
+      if (i < rk) v = c < rk ? (i == c ? T(1) : T(0)) : Ca[i * w + (c - rk)];
+      else v = c < rk ? T(0) : Rw[(i - rk) * w + (c - rk)];
+      R[t] = v;
+    }
+  } else if (blockIdx.x == 0) {
+    // A' = [U | W''] = Q R'; A = A' + [0 | U C] and U = Q R'[:, :rk], so R = R' + [0 | R'[:, :rk] C]
+    qr_body(m, ld, A, Q, R, tau);
+    __syncthreads();
+    for (int t = tid; t < rk * w; t += CT) {
+      const int i = t / w, j = t - i * w;
+      T sacc = T(0);
+      for (int k = i; k < rk; ++k) sacc += R[(size_t)i * ld + k] * Ca[k * w + j];
+      R[(size_t)i * ld + rk + j] += sacc;
+    }
+  }
+}
+
 }  // namespace
 
 size_t qr_work_elems(int m, int n) { return (size_t)std::min(m, n) + 8; }
@@ -405,6 +553,36 @@ void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
   qr_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, Q, R, work);
   count_launch(ctx);
   check_launch(ctx, "qr");
+}
+
+size_t qr_ext_work_elems(int m, int rk, int w) {
+  return 2 * (size_t)rk * w + 2 * (size_t)m * w + (size_t)w * w + (size_t)(rk + w) + 64 * (CT / 32) + 8;
+}
+
+template <typename T>
+void qr_ext(tnfem_ctx* ctx, int m, int rk, int w, T* A, T* Q, T* R, T* work, size_t work_elems) {
+  const int ld = rk + w;
+  if (w < 1 || rk < 1 || m < ld || work_elems < qr_ext_work_elems(m, rk, w)) {
+    qr<T>(ctx, m, ld, A, Q, R, work);
+    return;
+  }
+  GridBar* bar = reinterpret_cast<GridBar*>(ctx->scratch + kScratchDoubles - 512);
+  TN_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx->stream));
+  int dev_sms = 0;
+  TN_CHECK_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  int ncta = std::max(1, std::min({64, dev_sms, (rk * w + (CT / 32) - 1) / (CT / 32)}));
+  void* args[] = {&m, &rk, &w, &A, &Q, &R, &work, &bar};
+  {
+    ProfScope ps(ctx, TNFEM_PROF_QR, 8.0 * m * rk * (double)w, (double)(2 * m * ld + ld * ld) * sizeof(T));
+    TN_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(qr_ext_coop_kernel<T>), dim3(ncta), dim3(CT),
+                                              args, 0, ctx->stream));
+  }
+  count_launch(ctx);
+  check_launch(ctx, "qr");
+  int err = 0;
+  TN_CHECK_CUDA(cudaMemcpyAsync(&err, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  if (err) throw Error(TNFEM_E_TIMEOUT, "qr: a grid barrier wait expired");
 }
 
 // TNFEM_SVD_PROF set: Jacobi sweeps of every cooperative SVD, reported at process exit.
@@ -451,7 +629,7 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
     void* args[] = {&m, &n, &A, &U, &S, &Vt, &G, &V, &sig, &max_sweeps, &bar};
     {
       ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
-      TN_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(svd_coop_kernel<T>), dim3(ncta), dim3(32),
+      TN_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(svd_coop_kernel<T>), dim3(ncta), dim3(CT),
                                                 args, 0, ctx->stream));
     }
     count_launch(ctx);
@@ -488,6 +666,8 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
 template void qr<double>(tnfem_ctx*, int, int, double*, double*, double*, double*);
 template void qr<float>(tnfem_ctx*, int, int, float*, float*, float*, float*);
 template void svd<double>(tnfem_ctx*, int, int, double*, double*, double*, double*, double*);
+template void qr_ext<double>(tnfem_ctx*, int, int, int, double*, double*, double*, double*, size_t);
+template void qr_ext<float>(tnfem_ctx*, int, int, int, float*, float*, float*, float*, size_t);
 template void svd<float>(tnfem_ctx*, int, int, float*, float*, float*, float*, float*);
 
 }  // namespace tnfem

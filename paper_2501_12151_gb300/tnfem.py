@@ -114,6 +114,7 @@ _sig("tnfem_free_mpo", None, [_vp])
 _sig("tnfem_op_local_matvec", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_env_left", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_qr", _i, [_vp, _i, _i, _vp, _vp, _vp])
+_sig("tnfem_op_qr_ext", _i, [_vp, _i, _i, _i, _vp, _vp, _vp])
 _sig("tnfem_op_svd", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_local_matvec_noalloc", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _ll = C.c_longlong
@@ -395,6 +396,9 @@ class Context:
 
     def op_qr(self, m, n, A, Q, R):
         self.check(lib.tnfem_op_qr(self.h, m, n, A, Q, R))
+
+    def op_qr_ext(self, m, rk, w, A, Q, R):
+        self.check(lib.tnfem_op_qr_ext(self.h, m, rk, w, A, Q, R))
 
     def op_svd(self, m, n, A, U, S, Vt):
         self.check(lib.tnfem_op_svd(self.h, m, n, A, U, S, Vt))

@@ -88,6 +88,39 @@ def test_qr(ctx, m, n):
     np.testing.assert_allclose(sgn[:, None] * Rh, Rn, atol=1e-12 * np.abs(A).max() * max(m, n))
 
 
+def _qr_ext(ctx, A, rk, w):
+    m = A.shape[0]
+    ld = rk + w
+    Q = torch.zeros(m * ld, dtype=torch.float64, device="cuda")
+    R = torch.zeros(ld * ld, dtype=torch.float64, device="cuda")
+    tA = dev(A)
+    ctx.op_qr_ext(m, rk, w, tA.data_ptr(), Q.data_ptr(), R.data_ptr())
+    return Q.cpu().numpy().reshape(m, ld), R.cpu().numpy().reshape(ld, ld)
+
+
+# [U | W] with U orthonormal (the enrichment's basis): shapes of the sweep (m = r0 n, rk + kick)
+# and ragged ones; W general, W inside span(U) (the Householder fallback) and W partly inside
+@pytest.mark.parametrize("m,rk,w", [(196, 49, 4), (5, 1, 4), (36, 31, 4), (288, 72, 4), (64, 60, 4), (9, 2, 3)])
+@pytest.mark.parametrize("kind", ["general", "in_span", "partly"])
+def test_qr_ext(ctx, m, rk, w, kind):
+    r = W.rng(31 + m + rk)
+    U, _ = np.linalg.qr(r.standard_normal((m, rk)))
+    Wm = r.standard_normal((m, w))
+    if kind == "in_span":
+        Wm = U @ r.standard_normal((rk, w))
+    elif kind == "partly":
+        Wm[:, 0] = U @ r.standard_normal(rk)
+    A = np.hstack([U, Wm])
+    Qh, Rh = _qr_ext(ctx, A, rk, w)
+    ld = rk + w
+    scale = np.abs(A).max() * m
+    assert np.abs(Qh.T @ Qh - np.eye(ld)).max() <= 1e-12, kind
+    assert np.abs(Qh @ Rh - A).max() <= 1e-13 * scale, kind
+    assert np.abs(np.tril(Rh, -1)).max() <= 1e-13 * scale
+    # the span of [U | W] is kept: every column of A lies in span(Q)
+    assert np.abs(Qh @ (Qh.T @ A) - A).max() <= 1e-12 * scale
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (9, 4), (272, 68), (68, 68), (512, 128)])
 def test_svd(ctx, m, n):
     r = W.rng(11)
