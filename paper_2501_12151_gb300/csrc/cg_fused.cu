@@ -29,14 +29,15 @@
 // is small; the threads then form two groups that take alternate k of each chunk, and the groups'
 // accumulators are summed through shared memory at the end.
 //
-// A CG iteration thus costs three grid barriers and no launch.  Every barrier wait is bounded
-// (kWaitNs): on expiry the CTA records the error and leaves, and so does every other CTA at its
-// next barrier.
+// A CG iteration thus costs three grid barriers (two-level, see grid_sync.cuh) and no launch.
+// Every barrier wait is bounded: on expiry the CTA records the error and leaves, and so does every
+// other CTA at its next barrier.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 
 #include "cg_fused.h"
+#include "grid_sync.cuh"
 
 namespace tnfem {
 
@@ -44,22 +45,13 @@ namespace {
 
 constexpr int FT = 256;                      // threads per CTA
 constexpr int kTL = 64;                      // row stride of a staged tile chunk (elements)
-constexpr long long kWaitNs = 2000000000ll;  // 2 s bound on one barrier wait
 constexpr int kRCB = 8192;                   // binary32 preconditioner elements staged at once
 
 __host__ __device__ inline int rup4(int v) { return (v + 3) & ~3; }
 
-// Grid barrier state (in the ctl buffer): the top counter and generation, then one arrival
-// counter per group of CTAs, each on its own 128-byte line.
-struct FcgBar {
-  unsigned int count;
-  unsigned int gen;
-  int err;
-  int pad;
-};
-constexpr int kBarGroupsMax = 32;
-constexpr int kCtlInts = 64 + 32 * kBarGroupsMax;  // ints of the ctl buffer
-__host__ __device__ inline int bar_group_size(int ncta) { return (ncta + kBarGroupsMax - 1) / kBarGroupsMax; }
+// Grid barrier state in the ctl buffer (see grid_sync.cuh): GridSync at ctl + 4, one arrival
+// counter per group of CTAs at ctl + 64 + 32 g (separate 128-byte lines).
+constexpr int kCtlInts = 64 + 32 * kGridGroupsMax;  // ints of the ctl buffer
 
 // Staging sizes per precision: K chunk of phase 2 (double-buffered) and phase 1, and the elements
 // of one buffer of a PhiR slice (phase 2, second contraction).
@@ -113,53 +105,12 @@ struct FcgArgs {
   U* x;
   U* ws;          // packed operators and the iteration's vectors (fcg_dims layout)
   double* parts;  // pap [n2], rr [2][n3], rz [2][n3]
-  int* ctl;       // [0] state, [1] iterations; FcgBar at ctl + 4; group counters from ctl + 64
+  int* ctl;       // [0] state, [1] iterations; GridSync at ctl + 4; group counters from ctl + 64
   unsigned long long* tprof;  // nullable: SM cycles per phase summed over CTAs (7 slots), then passes
 };
 
-// true when every CTA arrived and none reported an error (one answer for the whole CTA: thread 0
-// reads the error flag and broadcasts it, so no CTA splits on a flag set between two reads).
-// Arrival is two-level: the CTAs of a group count on the group's line, the last of them on the top
-// counter, and the last group flips the generation the others poll; no counter sees more than
-// about 32 same-address atomics per barrier.
-__device__ __forceinline__ bool fcg_sync(int* ctl) {
-  __shared__ int s_ok;
-  FcgBar* bar = reinterpret_cast<FcgBar*>(ctl + 4);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    const unsigned int g0 = *vgen;
-    const int gsz = bar_group_size(gridDim.x);
-    const int grp = blockIdx.x / gsz;
-    const int ngrp = (gridDim.x + gsz - 1) / gsz;
-    const unsigned int in_grp = (unsigned int)min(gsz, (int)gridDim.x - grp * gsz);
-    unsigned int* gcount = reinterpret_cast<unsigned int*>(ctl + 64 + 32 * grp);
-    __threadfence();
-    bool flipped = false;
-    if (atomicAdd(gcount, 1u) == in_grp - 1) {
-      atomicExch(gcount, 0u);
-      if (atomicAdd(&bar->count, 1u) == (unsigned int)ngrp - 1) {
-        atomicExch(&bar->count, 0u);
-        __threadfence();
-        atomicAdd(&bar->gen, 1u);
-        flipped = true;
-      }
-    }
-    if (!flipped) {
-      const unsigned long long t0 = global_ns();
-      unsigned int spins = 0;
-      while (*vgen == g0) {
-        if ((++spins & 63u) == 0 && global_ns() - t0 > (unsigned long long)kWaitNs) {
-          atomicExch(&bar->err, 1);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = *((volatile int*)&bar->err) == 0;
-  }
-  __syncthreads();
-  return s_ok != 0;
+__device__ __forceinline__ bool fcg_sync(int* ctl, unsigned int& idx) {
+  return grid_sync_groups(reinterpret_cast<GridSync*>(ctl + 4), reinterpret_cast<unsigned int*>(ctl + 64), idx);
 }
 
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
@@ -476,6 +427,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
   U beta = U(0);
   int it = 0;
   int state = 0;
+  unsigned int bidx = 0;  // grid barriers passed
   // optional phase timing (thread 0 of every CTA): work and barrier wait of each phase
   const bool tp = A.tprof != nullptr && threadIdx.x == 0;
   long long tmark = tp ? clock64() : 0;
@@ -560,7 +512,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
       }
     }
     mark(0);
-    if (!fcg_sync(A.ctl)) return;
+    if (!fcg_sync(A.ctl, bidx)) return;
     mark(1);
 
     // ---- phase 2: per (a', g-slice) T2 = T1[a'] . A, then its share of B p and p.Bp --------------
@@ -665,7 +617,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
       }
     }
     mark(3);
-    if (!fcg_sync(A.ctl)) return;
+    if (!fcg_sync(A.ctl, bidx)) return;
     mark(4);
 
     // ---- phase 3: alpha; r -= alpha B p; z = M^{-1} r; x += alpha p; r.r and r.z shares -------------
@@ -789,7 +741,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
     }
     if (!first) ++it;
     mark(5);
-    if (!fcg_sync(A.ctl)) return;
+    if (!fcg_sync(A.ctl, bidx)) return;
 
     // ---- stop test and beta of the next pass -----------------------------------------------
     if (warp < 3) {
@@ -992,7 +944,8 @@ int FusedCg::run(tnfem_ctx* ctx, const FcgPlan& pl, int r0, int n, int r1, int a
   check_launch(ctx, "fused conjugate gradients");
   TN_CHECK_CUDA(cudaMemcpyAsync(host_, ctl_, 8 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
-  if (host_[4 + 2] != 0) throw Error(TNFEM_E_TIMEOUT, "fused conjugate gradients: a grid barrier wait expired");
+  if (static_cast<unsigned int>(host_[4 + 1]) & kGridErrBit)
+    throw Error(TNFEM_E_TIMEOUT, "fused conjugate gradients: a grid barrier wait expired");
   const int its = host_[1];
   *state = host_[0];
   if (prof_on_) {

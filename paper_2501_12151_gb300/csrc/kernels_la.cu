@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cfloat>
 
+#include "grid_sync.cuh"
 #include "internal.h"
 
 namespace tnfem {
@@ -281,53 +282,28 @@ __global__ void __launch_bounds__(LT) svd_kernel(int m, int n, const T* __restri
 // The same rotations as svd_kernel, but each pair of a round is handled by its own CTA (four warps),
 // so the binary64 work of a round is spread over as many SMs as there are pairs; rounds are
 // separated by a grid barrier.  The kernel is launched cooperatively (all CTAs resident), and
-// every barrier wait is bounded: on expiry the CTA sets err[0], and every CTA leaves at the next
+// every barrier wait is bounded: on expiry the CTA sets err, and every CTA leaves at the next
 // barrier check without writing outputs.
 
 struct GridBar {
-  unsigned int count;
-  unsigned int gen;
+  unsigned int count;  // GridSync: arrivals
+  unsigned int gen;    // GridSync: completed barriers | error bit
   int err;
   int rot[127];  // rotations per sweep (zeroed before the launch)
+  int prof;      // nonzero: svd_coop_kernel accumulates SM cycles per stage of a round into tcyc
+  int pad;
+  unsigned long long tcyc[6];  // sums over CTAs: sums, rotation, update, barrier, rounds, (spare)
 };
 
-constexpr long long kBarSpin = 1ll << 24;
+constexpr int CT = 128;  // threads per CTA of the cooperative kernels: four warps, all four SM partitions
 
-// true when all CTAs arrived and no CTA reported an error (thread 0 reads the flag and broadcasts
-// it, so the threads of a CTA cannot disagree)
-__device__ bool grid_barrier(GridBar* bar) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
-      bar->count = 0;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long it = 0;
-      while (*vgen == g) {
-        if (++it > kBarSpin) {
-          atomicExch(&bar->err, 1);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = *((volatile int*)&bar->err) == 0;
-  }
-  __syncthreads();
-  return s_ok != 0;
+// every wait bounded (see grid_sync.cuh); a failure is also recorded in err for the host
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& idx) {
+  const bool ok = grid_sync(reinterpret_cast<GridSync*>(bar), idx);
+  if (!ok && threadIdx.x == 0) atomicExch(&bar->err, 1);
+  return ok;
 }
 
-constexpr int CT = 128;  // threads per CTA of the cooperative SVD: four warps, all four SM partitions
-
-// One-sided Jacobi, one column pair per CTA and round (round-robin ordering), rounds separated by
-// grid barriers.  The four warps of a CTA split the column loops; the pair's three sums meet in
-// shared memory, thread 0 decides the rotation.  Rotate when |c| > tol sqrt(a b), tested as
-// c^2 > tol^2 a b (no square root) unless a or b is so small that the squares could underflow.
 template <typename T>
 __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
                                                       T* __restrict__ S, T* __restrict__ Vt, T* G, T* V, T* sig,
@@ -337,6 +313,7 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
   __shared__ int s_rot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x, ncta = gridDim.x;
+  unsigned int bidx = 0;  // grid barriers passed
   // copy-in: G column-major, V = I (rows spread over CTAs)
   for (long long t = (long long)cta * CT + tid; t < (long long)m * n; t += (long long)ncta * CT) {
     const int i = (int)(t / n), j = (int)(t % n);
@@ -346,13 +323,24 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
     const int i = (int)(t % n), j = (int)(t / n);
     V[t] = (i == j) ? T(1) : T(0);
   }
-  if (!grid_barrier(bar)) return;
+  if (!grid_barrier(bar, bidx)) return;
   const int np = n + (n & 1);
   const T tol = eps_of<T>() * (T)4;
   const T tiny = sizeof(T) == 8 ? T(1e-140) : T(1e-17);
   const int sweeps = min(max_sweeps, 127);
+  // optional stage timing (thread 0): sums, rotation, update, barrier
+  const bool tp = bar->prof != 0 && tid == 0;
+  long long tm = tp ? clock64() : 0, tc[5] = {0, 0, 0, 0, 0};
+  auto mark = [&](int slot) {
+    if (tp) {
+      const long long t = clock64();
+      tc[slot] += t - tm;
+      tm = t;
+    }
+  };
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     for (int r = 0; r < np - 1; ++r) {
+      if (tp) ++tc[4];
       for (int pi = cta; pi < np / 2; pi += ncta) {
         int p, q;
         if (pi == 0) { p = r; q = np - 1; }
@@ -373,6 +361,7 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
           red[2][warp] = c;
         }
         __syncthreads();
+        mark(0);
         if (tid == 0) {
           a = b = c = T(0);
           for (int w = 0; w < CT / 32; ++w) {
@@ -394,6 +383,7 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
           s_rot = rotate;
         }
         __syncthreads();
+        mark(1);
         if (!s_rot) continue;
         const T cs = s_cs, sn = s_sn;
         for (int i = tid; i < m; i += CT) {
@@ -408,11 +398,16 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
           vp[i] = cs * x - sn * y;
           vq[i] = sn * x + cs * y;
         }
+        __syncthreads();
+        mark(2);
       }
-      if (!grid_barrier(bar)) return;
+      if (!grid_barrier(bar, bidx)) return;
+      mark(3);
     }
     if (*((volatile int*)&bar->rot[sweep]) == 0) break;
   }
+  if (tp)
+    for (int i = 0; i < 5; ++i) atomicAdd(&bar->tcyc[i], (unsigned long long)tc[i]);
   // singular values, then (after a barrier) ranks, signs and outputs; columns spread over the
   // warps of all CTAs
   const int gw = cta * (CT / 32) + warp, nwarp = ncta * (CT / 32);
@@ -422,7 +417,7 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
     s = warp_sum(s);
     if (lane == 0) sig[j] = sqrt(s);
   }
-  if (!grid_barrier(bar)) return;
+  if (!grid_barrier(bar, bidx)) return;
   for (int j = gw; j < n; j += nwarp) {
     const T sj = sig[j];
     int pos = 0;
@@ -465,6 +460,7 @@ __global__ void __launch_bounds__(CT) qr_ext_coop_kernel(int m, int rk, int w, T
                                                          T* __restrict__ R, T* __restrict__ work, GridBar* bar) {
   const int ld = rk + w;
   const int tid = threadIdx.x, lane = tid & 31;
+  unsigned int bidx = 0;  // grid barriers passed
   const int gwarp = blockIdx.x * (CT / 32) + (tid >> 5), nwarp = gridDim.x * (CT / 32);
   const int gthr = blockIdx.x * CT + tid, nthr = gridDim.x * CT;
   T* Cp = work;                    // [rk][w] this pass's coefficients
@@ -487,21 +483,21 @@ __global__ void __launch_bounds__(CT) qr_ext_coop_kernel(int m, int rk, int w, T
         Ca[it] = pass == 0 ? sacc : Ca[it] + sacc;
       }
     }
-    if (!grid_barrier(bar)) return;
+    if (!grid_barrier(bar, bidx)) return;
     for (int t = gthr; t < m * w; t += nthr) {
       const int i = t / w, j = t - i * w;
       T sacc = T(0);
       for (int k = 0; k < rk; ++k) sacc += U[(size_t)i * ld + k] * Cp[k * w + j];
       W[(size_t)i * ld + j] -= sacc;
     }
-    if (!grid_barrier(bar)) return;
+    if (!grid_barrier(bar, bidx)) return;
   }
   if (blockIdx.x == 0) {
     for (int t = tid; t < m * w; t += CT) Wc[t] = W[(size_t)(t / w) * ld + t % w];
     __syncthreads();
     qr_body(m, w, Wc, Qw, Rw, tau);
   }
-  if (!grid_barrier(bar)) return;
+  if (!grid_barrier(bar, bidx)) return;
   // orthogonality of Q_w to U
   T mx = T(0);
   for (int it = gwarp; it < rk * w; it += nwarp) {
@@ -511,7 +507,7 @@ __global__ void __launch_bounds__(CT) qr_ext_coop_kernel(int m, int rk, int w, T
     mx = fmax(mx, fabs(warp_sum(sacc)));
   }
   if (lane == 0) emax[gwarp] = mx;
-  if (!grid_barrier(bar)) return;
+  if (!grid_barrier(bar, bidx)) return;
   T worst = T(0);
   for (int i = 0; i < nwarp; ++i) worst = fmax(worst, emax[i]);
   if (worst <= T(1e-10)) {
@@ -590,6 +586,7 @@ struct SvdStats {
   bool on = getenv("TNFEM_SVD_PROF") != nullptr;
   long long calls = 0, sweeps = 0, mn = 0;
   int hist[16] = {};
+  double cyc[5] = {};  // per CTA: sums, rotation, update, barrier cycles; rounds
   void add(int m, int n, int sw) {
     ++calls;
     sweeps += sw;
@@ -603,6 +600,9 @@ struct SvdStats {
     for (int i = 0; i < 16; ++i)
       if (hist[i]) fprintf(stderr, " %d:%d", i, hist[i]);
     fprintf(stderr, "\n");
+    if (cyc[4] > 0)
+      fprintf(stderr, "[tnfem] cooperative SVD SM cycles per round (mean over CTAs): sums %.0f rotation %.0f update %.0f barrier %.0f\n",
+              cyc[0] / cyc[4], cyc[1] / cyc[4], cyc[2] / cyc[4], cyc[3] / cyc[4]);
   }
 };
 SvdStats& svd_stats() {
@@ -621,6 +621,10 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
     // binary64 with enough pairs per round: spread the rounds over SMs
     GridBar* bar = reinterpret_cast<GridBar*>(ctx->scratch + kScratchDoubles - 512);
     TN_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx->stream));
+    if (svd_stats().on) {
+      const int one = 1;
+      TN_CHECK_CUDA(cudaMemcpyAsync(&bar->prof, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
     int ncta = (n + (n & 1)) / 2;
     int dev_sms = 0;
     TN_CHECK_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -645,6 +649,9 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
       int sw = 0;
       while (sw < max_sweeps && sw < 127 && rot[sw] != 0) ++sw;
       svd_stats().add(m, n, std::min(sw + 1, max_sweeps));
+      unsigned long long tc[6];
+      TN_CHECK_CUDA(cudaMemcpy(tc, bar->tcyc, sizeof(tc), cudaMemcpyDeviceToHost));
+      for (int i = 0; i < 5; ++i) svd_stats().cyc[i] += (double)tc[i] / ncta;
     }
     return;
   }
