@@ -8,6 +8,8 @@
 #include <cstdlib>
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "grid_sync.cuh"
 #include "internal.h"
 
@@ -445,6 +447,156 @@ __global__ void __launch_bounds__(CT) svd_coop_kernel(int m, int n, const T* __r
   }
 }
 
+// ---- one-sided Jacobi inside one thread-block cluster --------------------------------------------
+// The rotations of svd_coop_kernel, with every column resident in the shared memory of its owner
+// CTA (column j in CTA j mod C) and reached by the other CTAs of the cluster through distributed
+// shared memory; rounds are separated by the hardware cluster barrier instead of a grid barrier
+// in L2.  Each CTA has two groups of four warps, each group taking one column pair per round
+// (pairs b, b + 2C, ... for slot b = 2 rank + group), so C = ceil(pairs / 2) CTAs hold a round.
+// Every thread of every CTA runs the same rounds and sweeps (the stop decision reads one counter
+// after a cluster barrier), so the barrier counts agree by construction.
+constexpr int CLT = 256;  // threads per CTA of the cluster SVD: two groups of four warps
+
+template <typename T>
+__global__ void __launch_bounds__(CLT) svd_cluster_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ U,
+                                                          T* __restrict__ S, T* __restrict__ Vt, int max_sweeps) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cluster = cgr::this_cluster();
+  extern __shared__ __align__(16) unsigned char cl_smem[];
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int ncol = (n + C - 1) / C;           // columns owned per CTA (at most)
+  T* Gl = reinterpret_cast<T*>(cl_smem);      // [ncol][m]
+  T* Vl = Gl + (size_t)ncol * m;              // [ncol][n]
+  T* sig = Vl + (size_t)ncol * n;             // [n] (CTA 0's copy is the shared one)
+  __shared__ int rot[128];                    // rotations per sweep (CTA 0's copy is the shared one)
+  __shared__ T red[2][3][4];
+  __shared__ T s_cs[2], s_sn[2];
+  __shared__ int s_rot[2];
+  const int tid = threadIdx.x, grp = tid >> 7, gt = tid & 127, gw = gt >> 5, lane = tid & 31;
+  auto colG = [&](int j) -> T* { return cluster.map_shared_rank(Gl, j % C) + (size_t)(j / C) * m; };
+  auto colV = [&](int j) -> T* { return cluster.map_shared_rank(Vl, j % C) + (size_t)(j / C) * n; };
+  // the four warps of one group meet at a named barrier (ids 1, 2)
+  auto group_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory"); };
+  // copy-in of the owned columns, V = I
+  for (int lj = 0; lj * C + rank < n; ++lj) {
+    const int j = lj * C + rank;
+    for (int i = tid; i < m; i += CLT) Gl[(size_t)lj * m + i] = A[(size_t)i * n + j];
+    for (int i = tid; i < n; i += CLT) Vl[(size_t)lj * n + i] = i == j ? T(1) : T(0);
+  }
+  for (int i = tid; i < 128; i += CLT) rot[i] = 0;
+  cluster.sync();
+  int* rot0 = cluster.map_shared_rank(rot, 0);
+  const int np = n + (n & 1);
+  const int npairs = np / 2;
+  const T tol = eps_of<T>() * (T)4;
+  const T tiny = sizeof(T) == 8 ? T(1e-140) : T(1e-17);
+  const int sweeps = min(max_sweeps, 127);
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      for (int pi = 2 * rank + grp; pi < npairs; pi += 2 * C) {
+        int p, q;
+        if (pi == 0) { p = r; q = np - 1; }
+        else { p = (r + pi) % (np - 1); q = (r - pi + (np - 1)) % (np - 1); }
+        if (p >= n || q >= n) continue;  // uniform within the group
+        if (p > q) { int t = p; p = q; q = t; }
+        T* gp = colG(p);
+        T* gq = colG(q);
+        T a = T(0), b = T(0), c = T(0);
+        for (int i = gt; i < m; i += 128) {
+          T x = gp[i], y = gq[i];
+          a += x * x; b += y * y; c += x * y;
+        }
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (lane == 0) {
+          red[grp][0][gw] = a;
+          red[grp][1][gw] = b;
+          red[grp][2][gw] = c;
+        }
+        group_sync();
+        if (gt == 0) {
+          a = (red[grp][0][0] + red[grp][0][1]) + (red[grp][0][2] + red[grp][0][3]);
+          b = (red[grp][1][0] + red[grp][1][1]) + (red[grp][1][2] + red[grp][1][3]);
+          c = (red[grp][2][0] + red[grp][2][1]) + (red[grp][2][2] + red[grp][2][3]);
+          int rotate = 0;
+          if (c != T(0) && a != T(0) && b != T(0)) {
+            rotate = (a > tiny && b > tiny) ? (c * c > tol * tol * a * b) : (fabs(c) > tol * sqrt(a * b));
+          }
+          if (rotate) {
+            T cs, sn;
+            jacobi_rotation(a, b, c, cs, sn);
+            s_cs[grp] = cs;
+            s_sn[grp] = sn;
+            atomicAdd(rot0 + sweep, 1);
+          }
+          s_rot[grp] = rotate;
+        }
+        group_sync();
+        if (s_rot[grp]) {
+          const T cs = s_cs[grp], sn = s_sn[grp];
+          for (int i = gt; i < m; i += 128) {
+            T x = gp[i], y = gq[i];
+            gp[i] = cs * x - sn * y;
+            gq[i] = sn * x + cs * y;
+          }
+          T* vp = colV(p);
+          T* vq = colV(q);
+          for (int i = gt; i < n; i += 128) {
+            T x = vp[i], y = vq[i];
+            vp[i] = cs * x - sn * y;
+            vq[i] = sn * x + cs * y;
+          }
+        }
+        group_sync();  // red / s_* are reused by the group's next pair
+      }
+      cluster.sync();
+    }
+    const int done = *((volatile int*)(rot0 + sweep)) == 0;
+    if (done) break;
+  }
+  // singular values of the owned columns into CTA 0's sig, then ranks, signs and outputs
+  T* sig0 = cluster.map_shared_rank(sig, 0);
+  const int warp = tid >> 5, nw = CLT / 32;
+  for (int lj = warp; lj * C + rank < n; lj += nw) {
+    const int j = lj * C + rank;
+    const T* g = Gl + (size_t)lj * m;
+    T sacc = T(0);
+    for (int i = lane; i < m; i += 32) sacc += g[i] * g[i];
+    sacc = warp_sum(sacc);
+    if (lane == 0) sig0[j] = sqrt(sacc);
+  }
+  cluster.sync();
+  for (int lj = warp; lj * C + rank < n; lj += nw) {
+    const int j = lj * C + rank;
+    const T* g = Gl + (size_t)lj * m;
+    const T* v = Vl + (size_t)lj * n;
+    const T sj = sig0[j];
+    int pos = 0;
+    for (int i = lane; i < n; i += 32) {
+      const T si = sig0[i];
+      pos += (si > sj || (si == sj && i < j)) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+    T best = T(-1);
+    int bi = 0;
+    for (int i = lane; i < m; i += 32) {
+      const T val = fabs(g[i]);
+      if (val > best) { best = val; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const T sgn = (g[bi] < T(0)) ? T(-1) : T(1);
+    const T inv = sj > T(0) ? sgn / sj : T(0);
+    for (int i = lane; i < m; i += 32) U[(size_t)i * n + pos] = g[i] * inv;
+    for (int i = lane; i < n; i += 32) Vt[(size_t)pos * n + i] = sgn * v[i];
+    if (lane == 0) S[pos] = sj;
+  }
+  cluster.sync();  // CTA 0's sig and rot stay alive until every CTA is done reading them
+}
+
 // ---- QR of [U | W] with U orthonormal ---------------------------------------------------------
 // Q, R of the m x (rk + w) matrix A = [U | W] (row-major, leading dimension rk + w) when its first
 // rk columns are orthonormal (the left singular vectors of the sweep's truncation, step a7): W is
@@ -610,6 +762,59 @@ SvdStats& svd_stats() {
   return st;
 }
 
+// The binary64 SVD on one thread-block cluster (svd_cluster_kernel); false when the shape or the
+// device does not allow it (more than 16 CTAs, shared memory, no cluster of that size resident),
+// and the caller takes the cooperative kernel.
+template <typename T>
+bool svd_cluster(tnfem_ctx* ctx, int m, int n, const T* A, T* U, T* S, T* Vt, int max_sweeps) {
+  const int np = n + (n & 1);
+  const int C = (np / 2 + 1) / 2;
+  if (C < 2 || C > 16) return false;
+  const int ncol = (n + C - 1) / C;
+  const size_t smem = ((size_t)ncol * (m + n) + n) * sizeof(T);
+  constexpr size_t kMax = 160 * 1024;
+  if (smem > kMax) return false;
+  static unsigned long long attr_set = 0;  // one bit per device
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (!(attr_set & bit)) {
+    if (cudaFuncSetAttribute(svd_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(svd_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr_set |= bit;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(CLT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, svd_cluster_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  {
+    ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
+    if (cudaLaunchKernelEx(&cfg, svd_cluster_kernel<T>, m, n, A, U, S, Vt, max_sweeps) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  count_launch(ctx);
+  check_launch(ctx, "svd");
+  return true;
+}
+
 template <typename T>
 void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   if (m <= 0 || n <= 0) return;
@@ -617,6 +822,7 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   T* G = work;
   T* V = G + (size_t)m * n;
   T* sig = V + (size_t)n * n;
+  if (sizeof(T) == 8 && n >= kSvdCoopMinN && !svd_stats().on && svd_cluster<T>(ctx, m, n, A, U, S, Vt, 60)) return;
   if (sizeof(T) == 8 && n >= kSvdCoopMinN) {
     // binary64 with enough pairs per round: spread the rounds over SMs
     GridBar* bar = reinterpret_cast<GridBar*>(ctx->scratch + kScratchDoubles - 512);

@@ -121,7 +121,10 @@ def test_qr_ext(ctx, m, rk, w, kind):
     assert np.abs(Qh @ (Qh.T @ A) - A).max() <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("m,n", [(1, 1), (9, 4), (272, 68), (68, 68), (512, 128)])
+# (1, 1), (9, 4): one CTA; (196, 49), (100, 16), (64, 63), (300, 33), (49, 49): one thread-block
+# cluster (16 <= n <= 64); (272, 68), (68, 68), (512, 128): the cooperative multi-CTA kernel
+@pytest.mark.parametrize("m,n", [(1, 1), (9, 4), (196, 49), (100, 16), (64, 63), (300, 33), (49, 49),
+                                 (272, 68), (68, 68), (512, 128)])
 def test_svd(ctx, m, n):
     r = W.rng(11)
     # graded singular values down to 1e-12 to exercise the truncation range
