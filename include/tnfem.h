@@ -328,6 +328,19 @@ tnfem_status tnfem_op_local_cg(tnfem_ctx* ctx, int precision, int precond, int r
  * tnfem_op_gemm_f32: C(b,m,n) = alpha sum_k A(b,m,k) B(b,k,n) + beta C(b,m,n) with element
  * (b,m,k) of A at A[b*sAb + m*sAm + k*sAk] (likewise B and C); every pointer is a device pointer to
  * binary32.  tnfem_op_local_matvec_f32: the contraction of tnfem_op_local_matvec in binary32. */
+/* Binary64 GEMM of tnfem_op_gemm_f32's layout (every pointer a device pointer to binary64).
+ * engine 0: binary64 FMA.  engine 1: double-binary32 arithmetic, the mixed-precision sweep's route
+ * for large contractions on this part (binary64 issues at 1/64 of the binary32 rate): operands
+ * split into (hi, lo) binary32 pairs, products carried with their exact rounding errors, sums as
+ * binary32 pairs with two-sum error recovery; relative error about K * 2^-47 of the sum of |terms|
+ * (binary64: K * 2^-53).  Engine 1 applies only to products of at least 2^20 multiply-adds
+ * (smaller ones run in binary64) and returns TNFEM_E_INVALID if a value leaves the binary32 range.
+ * The solve does not use engine 1: in the sweep its noise, amplified by the local systems'
+ * conditioning, kept the relative core updates from falling below a 1e-9 tolerance. */
+tnfem_status tnfem_op_gemm_f64(tnfem_ctx* ctx, int engine, int M, int N, int K, int batch, long long sAm,
+                               long long sAk, long long sAb, long long sBk, long long sBn, long long sBb,
+                               long long sCm, long long sCn, long long sCb, double alpha, const double* A,
+                               const double* B, double beta, double* C);
 tnfem_status tnfem_op_gemm_f32(tnfem_ctx* ctx, int engine, int M, int N, int K, int batch, long long sAm,
                                long long sAk, long long sAb, long long sBk, long long sBn, long long sBb,
                                long long sCm, long long sCn, long long sCb, float alpha, const float* A,

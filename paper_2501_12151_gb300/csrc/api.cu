@@ -25,6 +25,14 @@ struct EngineScope {
   ~EngineScope() { ctx->tensor_cores = saved; }
 };
 
+// large binary64 GEMMs in double-binary32 arithmetic for the scope's duration
+struct DfScope {
+  tnfem_ctx* ctx;
+  bool saved;
+  DfScope(tnfem_ctx* c, bool on) : ctx(c), saved(c->df64) { c->df64 = on; }
+  ~DfScope() { ctx->df64 = saved; }
+};
+
 template <typename F>
 tnfem_status guard(tnfem_ctx* ctx, F&& f) {
   try {
@@ -755,6 +763,28 @@ tnfem_status tnfem_op_local_cg(tnfem_ctx* ctx, int precision, int precond, int r
       tnfem::op_local_cg<float>(ctx, precond, r0, n, r1, a0, a1, (const float*)PhiL, (const float*)A, (const float*)PhiR,
                          (const float*)g, (float*)x, rtol, maxit, iters, state);
     sync(ctx);
+  });
+}
+
+tnfem_status tnfem_op_gemm_f64(tnfem_ctx* ctx, int engine, int M, int N, int K, int batch, long long sAm,
+                               long long sAk, long long sAb, long long sBk, long long sBn, long long sBb,
+                               long long sCm, long long sCn, long long sCb, double alpha, const double* A,
+                               const double* B, double beta, double* C) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    TN_REQUIRE(A && B && C, "null pointer");
+    TN_REQUIRE(engine == 0 || engine == 1, "engine must be 0 (binary64) or 1 (double-binary32)");
+    TN_REQUIRE(M >= 1 && N >= 1 && K >= 1 && batch >= 1, "sizes must be positive");
+    DfScope dfs(ctx, engine == 1);
+    GemmDesc g{M, N, K, batch, sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb};
+    const size_t work = (size_t)64 * batch * M * N;
+    DArr<double> w(ctx, std::min<size_t>(work, (size_t)1 << 25));
+    TN_CHECK_CUDA(cudaMemsetAsync(df_overflow_flag(ctx), 0, sizeof(int), ctx->stream));
+    gemm<double>(ctx, g, alpha, A, B, beta, C, w.p, w.n);
+    int ovf = 0;
+    TN_CHECK_CUDA(cudaMemcpyAsync(&ovf, df_overflow_flag(ctx), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    TN_REQUIRE(ovf == 0, "double-binary32 GEMM: a value outside the binary32 range");
   });
 }
 

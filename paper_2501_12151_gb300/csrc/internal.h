@@ -58,6 +58,7 @@ struct tnfem_ctx {
   };
   bool capturing = false;  // launches are being captured into a graph
   bool tensor_cores = false;  // binary32 GEMMs on tcgen05 (three-term TF32) instead of CUDA cores
+  bool df64 = false;          // large binary64 GEMMs in double-binary32 arithmetic (gemm_df_kernel)
   bool own_stream = false; // `stream` was created by the context (caller passed NULL)
   int prof_every = 0;
   long long prof_seen[TNFEM_PROF_CLASSES] = {};
@@ -81,6 +82,11 @@ struct tnfem_ctx {
 namespace tnfem {
 
 constexpr int kScratchDoubles = 1 << 16;
+// binary64 GEMMs with at least this many multiply-adds run in double-binary32 when ctx->df64
+// (tnfem_op_gemm_f64 engine 1; the solve does not use it, see the engine's description)
+constexpr double kDfMinMnk = 1 << 20;
+// device flag (in the context's scratch) set by a double-binary32 GEMM whose output was not finite
+inline int* df_overflow_flag(tnfem_ctx* ctx) { return reinterpret_cast<int*>(ctx->scratch + kScratchDoubles - 520); }
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs: partial sums of one reduction
 
 void* dalloc(tnfem_ctx* ctx, size_t bytes);

@@ -127,6 +127,154 @@ __global__ void __launch_bounds__(GT) gemm_kernel(GemmDesc g, T alpha, const T* 
   ktimer_end(timer);
 }
 
+// ---- binary64 GEMM in double-binary32 arithmetic ---------------------------------------------
+//
+// GB300 issues binary64 FMAs at 1/64 of the binary32 rate, so the large binary64 contractions of
+// the mixed-precision sweep can run faster as pairs of binary32 numbers: every operand is split as
+// x = hi + lo (hi = x rounded to binary32, lo = the binary32 rounding of the remainder, 48
+// significant bits together), every product as a b = p + e with p = hi_a hi_b rounded and e its
+// exact rounding error (an FMA) plus the cross terms hi_a lo_b + lo_a hi_b, and the sum is carried
+// as (S, s): S the binary32 running sum of the p (each addition's exact rounding error recovered
+// by a two-sum) and s the binary32 sum of those errors and the e.  About twelve binary32
+// operations per multiply-add; the relative error of a K-term sum is about K * 2^-47 of the sum of
+// |terms| (the dropped lo_a lo_b and the roundings of the small terms), against K * 2^-53 for
+// binary64.  Every operation is an explicitly rounded intrinsic so that no FMA contraction can
+// change the two-sum.  Values must stay inside the binary32 range: an output that is not finite
+// sets *overflow, and the caller then redoes the work in binary64.
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ void df_mac(float& S, float& s, const float2 a, const float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float t = __fadd_rn(S, p);
+  const float z = __fsub_rn(t, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = __fadd_rn(s, __fadd_rn(err, e));
+  S = t;
+}
+
+// gemm_kernel<double> with the operands staged as (hi, lo) pairs and the sums in double-binary32
+__global__ void __launch_bounds__(GT) gemm_df_kernel(GemmDesc g, double alpha, const double* __restrict__ A,
+                                                     const double* __restrict__ B, double beta,
+                                                     double* __restrict__ C, double* __restrict__ work,
+                                                     int splits, int kchunk, int flat, const int* __restrict__ skip,
+                                                     KTimer* __restrict__ timer, int* __restrict__ overflow) {
+  if (skip && *skip) return;
+  ktimer_begin(timer);
+  __shared__ float2 As[BK][BM + 1];
+  __shared__ float2 Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int bz = blockIdx.z;
+  const int b = flat ? 0 : bz / splits, sp = bz % splits;
+  const int kbeg = sp * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const long long rows = flat ? (long long)g.M * g.batch : g.M;
+  const double* Ab = A + (long long)b * g.sAb;
+  const double* Bb = B + (long long)b * g.sBb;
+  const bool a_k_fast = (g.sAk == 1);
+  const bool b_n_fast = (g.sBn == 1);
+  long long a_off[4];
+  bool a_ok[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int idx = tid + i * GT;
+    const int mm = a_k_fast ? idx / BK : idx % BM;
+    const long long R = m0 + mm;
+    a_ok[i] = R < rows;
+    const long long bb = flat ? R / g.M : 0, m = flat ? R - bb * g.M : R;
+    a_off[i] = bb * g.sAb + m * g.sAm;
+  }
+  float accS[4][4], accs[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      accS[i][j] = 0.0f;
+      accs[i][j] = 0.0f;
+    }
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int idx = tid + i * GT;
+      int mm, kk;
+      if (a_k_fast) { kk = idx % BK; mm = idx / BK; } else { mm = idx % BM; kk = idx / BM; }
+      int gk = k0 + kk;
+      double v = 0.0;
+      if (a_ok[i] && gk < kend) v = Ab[a_off[i] + (long long)gk * g.sAk];
+      As[kk][mm] = df_split(v);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int idx = tid + i * GT;
+      int nn, kk;
+      if (b_n_fast) { nn = idx % BN; kk = idx / BN; } else { kk = idx % BK; nn = idx / BK; }
+      int gn = n0 + nn, gk = k0 + kk;
+      double v = 0.0;
+      if (gn < g.N && gk < kend) v = Bb[(long long)gk * g.sBk + (long long)gn * g.sBn];
+      Bs[kk][nn] = df_split(v);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      float2 a[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_mac(accS[i][j], accs[i][j], a[i], bv[j]);
+    }
+    __syncthreads();
+  }
+  bool bad = false;
+  if (splits == 1) {
+    double* Cb = C + (long long)b * g.sCb;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long R = m0 + ty + 16 * i;
+      if (R >= rows) continue;
+      const long long bb = flat ? R / g.M : 0, m = flat ? R - bb * g.M : R;
+      double* crow = Cb + bb * g.sCb + m * g.sCm;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gn = n0 + tx + 16 * j;
+        if (gn >= g.N) continue;
+        double* c = crow + (long long)gn * g.sCn;
+        double v = alpha * ((double)accS[i][j] + (double)accs[i][j]);
+        if (beta != 0.0) v += beta * (*c);
+        bad |= !isfinite(v);
+        *c = v;
+      }
+    }
+  } else {
+    double* W = work + ((long long)sp * g.batch + b) * (long long)g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long R = m0 + ty + 16 * i;
+      if (R >= rows) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gn = n0 + tx + 16 * j;
+        if (gn >= g.N) continue;
+        const double v = (double)accS[i][j] + (double)accs[i][j];
+        bad |= !isfinite(v);
+        W[R * g.N + gn] = v;
+      }
+    }
+  }
+  if (bad && overflow) atomicExch(overflow, 1);
+  ktimer_end(timer);
+}
+
 template <typename T>
 __global__ void splitk_reduce_kernel(GemmDesc g, T alpha, T beta, T* __restrict__ C,
                                      const T* __restrict__ work, int splits,
@@ -326,7 +474,16 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
     const int cls = sizeof(T) == 8 ? TNFEM_PROF_CONTRACT64 : TNFEM_PROF_CONTRACT32;
     KTimer* timer = prof_ktimer(ctx, cls, 2.0 * mnk, words * sizeof(T));
     ProfScope ps(ctx, cls, 2.0 * mnk, words * sizeof(T), timer != nullptr);
-    gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip, timer);
+    if constexpr (sizeof(T) == 8) {
+      if (ctx->df64 && mnk >= kDfMinMnk) {
+        gemm_df_kernel<<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip, timer,
+                                                     df_overflow_flag(ctx));
+      } else {
+        gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip, timer);
+      }
+    } else {
+      gemm_kernel<T><<<grid, GT, 0, ctx->stream>>>(g, alpha, A, B, beta, C, work, splits, kchunk, flat, skip, timer);
+    }
   }
   count_launch(ctx);
   if (splits > 1) {

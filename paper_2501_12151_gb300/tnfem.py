@@ -119,6 +119,7 @@ _sig("tnfem_op_svd", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_local_matvec_noalloc", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _ll = C.c_longlong
 _sig("tnfem_op_gemm_f32", _i, [_vp, _i, _i, _i, _i, _i] + [_ll] * 9 + [C.c_float, _vp, _vp, C.c_float, _vp])
+_sig("tnfem_op_gemm_f64", _i, [_vp, _i, _i, _i, _i, _i] + [_ll] * 9 + [C.c_double, _vp, _vp, C.c_double, _vp])
 _sig("tnfem_op_local_matvec_f32", _i, [_vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp])
 _sig("tnfem_op_local_cg", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, C.c_double, _i,
                                C.POINTER(C.c_int), C.POINTER(C.c_int)])
@@ -382,6 +383,9 @@ class Context:
 
     def op_gemm_f32(self, engine, M, N, K, batch, strides, alpha, A, B, beta, Cp):
         self.check(lib.tnfem_op_gemm_f32(self.h, engine, M, N, K, batch, *strides, alpha, A, B, beta, Cp))
+
+    def op_gemm_f64(self, engine, M, N, K, batch, strides, alpha, A, B, beta, Cp):
+        self.check(lib.tnfem_op_gemm_f64(self.h, engine, M, N, K, batch, *strides, float(alpha), A, B, float(beta), Cp))
 
     def op_local_matvec_f32(self, engine, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y):
         self.check(lib.tnfem_op_local_matvec_f32(self.h, engine, r0, n, r1, a0, a1, PhiL, A, PhiR, x, y))

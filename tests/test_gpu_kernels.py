@@ -88,6 +88,61 @@ def test_qr(ctx, m, n):
     np.testing.assert_allclose(sgn[:, None] * Rh, Rn, atol=1e-12 * np.abs(A).max() * max(m, n))
 
 
+# binary64 GEMM engines: 0 binary64 FMA, 1 double-binary32 (hi/lo binary32 pairs; the
+# mixed-precision sweep's route for large contractions).  Error bounds relative to the sum of
+# |terms|: binary64 K * 2^-52, double-binary32 K * 2^-45 (its products and sums keep ~47 bits).
+GEMM64_CASES = [
+    (49, 204, 204, 49, "m", True),     # stage 2 of the working-shape local matvec (rows span batches)
+    (2499, 196, 49, 1, "k", True),     # stage 1
+    (196, 49, 2499, 1, "k", True),     # stage 3 (split K)
+    (300, 200, 70, 1, "m", True),
+    (64, 96, 40, 3, "k", False),       # per-batch B (below the 2^20 threshold: binary64 either way)
+    (130, 257, 260, 2, "k", False),
+]
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("M,N,K,batch,alay,shared", GEMM64_CASES)
+def test_gemm_f64_engines(ctx, engine, M, N, K, batch, alay, shared):
+    r = W.rng(200 + M + N + K)
+    A = r.standard_normal((batch, M, K)) if alay == "k" else r.standard_normal((batch, K, M))
+    Bb = 1 if shared else batch
+    # magnitudes of the sweep's operands (environments ~1e11, cores ~1), signed
+    B = r.standard_normal((Bb, K, N)) * 1e5
+    C0 = r.standard_normal((batch, M, N))
+    alpha, beta = 1.25, (0.0 if M % 2 else -0.5)
+    if alay == "k":
+        sAm, sAk, sAb = K, 1, M * K
+        Am = A
+    else:
+        sAm, sAk, sAb = 1, M, M * K
+        Am = A.transpose(0, 2, 1)
+    sBk, sBn, sBb = N, 1, (0 if shared else K * N)
+    strides = (sAm, sAk, sAb, sBk, sBn, sBb, N, 1, M * N)
+    tA, tB, tC = (dev(v) for v in (A, B, C0))
+    ctx.op_gemm_f64(engine, M, N, K, batch, strides, alpha, tA.data_ptr(), tB.data_ptr(), beta, tC.data_ptr())
+    got = tC.cpu().numpy()
+    Bf = np.broadcast_to(B, (batch, K, N))
+    ref = alpha * np.matmul(Am, Bf) + beta * C0
+    scale = abs(alpha) * np.matmul(np.abs(Am), np.abs(Bf)) + abs(beta) * np.abs(C0)
+    tol = K * (2.0 ** -52 if engine == 0 else 2.0 ** -45)
+    assert np.all(np.abs(got - ref) <= tol * scale + 1e-300)
+
+
+def test_gemm_f64_df_out_of_range(ctx):
+    from paper_2501_12151_gb300 import tnfem
+    # products beyond the binary32 range are reported, not returned as garbage
+    M, N, K = 128, 128, 128
+    A = np.full((M, K), 1e25)
+    B = np.full((K, N), 1e25)
+    Cm = torch.zeros(M * N, dtype=torch.float64, device="cuda")
+    strides = (K, 1, M * K, N, 1, K * N, N, 1, M * N)
+    with pytest.raises(tnfem.TnfemError):
+        ctx.op_gemm_f64(1, M, N, K, 1, strides, 1.0, dev(A).data_ptr(), dev(B).data_ptr(), 0.0, Cm.data_ptr())
+    ctx.op_gemm_f64(0, M, N, K, 1, strides, 1.0, dev(A).data_ptr(), dev(B).data_ptr(), 0.0, Cm.data_ptr())
+    assert np.allclose(Cm.cpu().numpy(), 128e50)
+
+
 def _qr_ext(ctx, A, rk, w):
     m = A.shape[0]
     ld = rk + w
