@@ -105,7 +105,7 @@ typedef struct {
   int tensor_cores;    /* MIXED / MIXED_LOCAL: 1 runs the binary32 contractions on the tcgen05
                           tensor cores (TF32 split products), 0 on CUDA-core FMA */
   double local_rtol;   /* each local solve stops at max(tol / 2, local_rtol * its starting relative
-                          residual); 0 solves every local system to tol / 2.  Default 1e-2 when the
+                          residual); 0 solves every local system to tol / 2.  Default 0.1 when the
                           field is negative */
   int cg_engine;       /* local solves: 0 one persistent cooperative kernel per solve (default),
                           1 one launch per conjugate-gradient step (graph-replayed chunks) */

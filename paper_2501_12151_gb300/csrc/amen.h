@@ -15,6 +15,9 @@ struct AmenSource {
   double coef = 1.0;
 };
 
+// Default fraction of a local system's starting residual to which it is solved (see AmenParams)
+constexpr double kLocalRtolDefault = 0.1;
+
 struct AmenParams {
   double tol = 1e-10;       // stop when the largest local residual or local update is <= tol
   int rmax = 64;            // rank cap
@@ -22,7 +25,7 @@ struct AmenParams {
   int max_sweeps = 40;
   int local_maxit = 500;    // conjugate-gradient iterations per local solve
   double resid_damp = 2.0;  // local solves stop at tol / resid_damp ...
-  double local_rtol = 1e-2; // ... or at local_rtol times their starting residual, whichever is larger
+  double local_rtol = kLocalRtolDefault;  // ... or at local_rtol times their starting residual, whichever is larger
   bool precond = true;      // block-Jacobi preconditioned conjugate gradients for the local solves
   bool local_mixed = false; // binary64 sweep with binary32 local solves refined in binary64
   bool graphs = true;       // replay the conjugate-gradient chunks as CUDA graphs

@@ -183,7 +183,7 @@ tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, con
   ip.local_maxit = o->local_maxit > 0 ? o->local_maxit : 500;
   ip.seed = o->seed;
   ip.precond = o->no_precond == 0;
-  ip.local_rtol = o->local_rtol < 0 ? 1e-2 : o->local_rtol;
+  ip.local_rtol = o->local_rtol < 0 ? kLocalRtolDefault : o->local_rtol;
   ip.fused_cg = o->cg_engine == 0;
   ip.verbose = getenv("TNFEM_VERBOSE") != nullptr;
   tnfem_tt* u = x0 ? tt_clone(x0) : nullptr;
@@ -431,7 +431,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
       p.local_maxit = opts->local_maxit > 0 ? opts->local_maxit : 500;
       p.seed = opts->seed;
       p.precond = opts->no_precond == 0;
-      p.local_rtol = opts->local_rtol < 0 ? 1e-2 : opts->local_rtol;
+      p.local_rtol = opts->local_rtol < 0 ? kLocalRtolDefault : opts->local_rtol;
       p.fused_cg = opts->cg_engine == 0;
       p.local_mixed = opts->precision == TNFEM_MIXED_LOCAL;
       p.verbose = getenv("TNFEM_VERBOSE") != nullptr;
