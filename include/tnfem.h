@@ -238,6 +238,13 @@ tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_gr
 tnfem_status tnfem_energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u,
                                const tnfem_tt* v, double* out);
 
+/* a9's confirmation: the global relative residual ||f - A u||_2 / ||f||_2 in binary64, from the
+ * explicitly formed residual train (A u by the MPO-TT product, ranks a_k r_k, then f - A u by
+ * concatenation) whose norm is taken from the orthogonalised train, so it does not cancel.  Its
+ * cost grows with (a r)^3 per core: intended for checks at small and moderate sizes. */
+tnfem_status tnfem_residual_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u,
+                                 double* out);
+
 /* <x, y> and ||x|| (norm from the orthogonalised train). */
 tnfem_status tnfem_tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y, double* out);
 tnfem_status tnfem_tt_norm(tnfem_ctx* ctx, const tnfem_tt* x, double* out);

@@ -568,6 +568,28 @@ tnfem_status tnfem_tt_norm(tnfem_ctx* ctx, const tnfem_tt* x, double* out) {
   });
 }
 
+tnfem_status tnfem_residual_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u,
+                                 double* out) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    TN_REQUIRE(A && f && u && out, "null argument");
+    tnfem_tt* Au = mpo_apply(ctx, A, u);
+    tnfem_tt* r = nullptr;
+    try {
+      r = tt_axpy(ctx, f, -1.0, Au);
+      const double rn = tt_norm(ctx, r);
+      const double fn = tt_norm(ctx, f);
+      *out = fn > 0 ? rn / fn : rn;
+    } catch (...) {
+      tnfem_free_tt(Au);
+      tnfem_free_tt(r);
+      throw;
+    }
+    tnfem_free_tt(Au);
+    tnfem_free_tt(r);
+  });
+}
+
 tnfem_status tnfem_tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax, tnfem_tt** out) {
   if (!ctx || !out) return TNFEM_E_INVALID;
   *out = nullptr;
