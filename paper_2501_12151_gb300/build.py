@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtnfem.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC] + ARCH
 
 
@@ -70,7 +70,7 @@ def build(verbose: bool = False, jobs: int = 0) -> str:
             if verbose and msg:
                 print(msg)
     if cmds or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        link = [nvcc, "-shared", "-o", LIB] + objs + ARCH + ["-lcudart"]
+        link = [nvcc, "-shared", "-o", LIB] + objs + ARCH + ["-lcudart", "-lpthread"]
         run(link)
     return LIB
 

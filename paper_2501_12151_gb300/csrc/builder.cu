@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <future>
 
 #include "builder.h"
 #include "internal.h"
@@ -366,6 +367,7 @@ AxisOps axis_operators(int L, double lo, double hi, const std::vector<double>& w
   AxisOps ops;
   ops.names = {"K", "M", "G", "GT", "I", "P"};
   std::vector<HTrain> trains;
+  std::vector<std::future<HTrain>> parts;
   for (const auto& name : ops.names) {
     std::vector<double> m(n, 0.0), s(n, 0.0), t(n, 0.0);
     for (int i = 0; i < n; ++i) {
@@ -392,8 +394,10 @@ AxisOps axis_operators(int L, double lo, double hi, const std::vector<double>& w
       }
     }
     ops.diag1.push_back(m[std::min(1, n - 1)]);  // entry (1,1), used for the shift s
-    trains.push_back(tridiag_mpo(m, s, t, L));
+    // the six 1D operators are independent: their TT-SVDs and roundings run on host threads
+    parts.push_back(std::async(std::launch::async, [m, s, t, L] { return tridiag_mpo(m, s, t, L); }));
   }
+  for (auto& f : parts) trains.push_back(f.get());
   ops.joint = stack_trains(trains);
   ops.joint.round(1e-15, 1 << 20);
   return ops;
@@ -498,31 +502,48 @@ HTrain combine_axes(const std::vector<HTrain>& axes, const std::vector<SepTerm>&
     }
     out.c.push_back(c1);
   }
-  // remaining level cores: Kronecker products of axis cores
-  for (int k = 2; k <= L; ++k) {
-    int R0 = 1, R1 = 1;
-    for (int d = 0; d < D; ++d) { R0 *= axes[d].c[k].r0; R1 *= axes[d].c[k].r1; }
-    HCore ck{R0, Q, R1, std::vector<double>((size_t)R0 * Q * R1, 0.0)};
-    std::vector<int> a(D), loc(D), b(D);
-    for (long long l = 0; l < (long long)R0; ++l) {
-      long long rem = l;
-      for (int d = D - 1; d >= 0; --d) { a[d] = (int)(rem % axes[d].c[k].r0); rem /= axes[d].c[k].r0; }
-      for (long long mm = 0; mm < (long long)Q; ++mm) {
-        long long rm = mm;
-        for (int d = D - 1; d >= 0; --d) { loc[d] = (int)(rm % q); rm /= q; }
-        for (long long rr2 = 0; rr2 < (long long)R1; ++rr2) {
-          long long r3 = rr2;
-          double v = 1.0;
-          for (int d = D - 1; d >= 0; --d) { b[d] = (int)(r3 % axes[d].c[k].r1); r3 /= axes[d].c[k].r1; }
-          for (int d = 0; d < D && v != 0.0; ++d) {
-            const HCore& c = axes[d].c[k];
-            v *= c.v[((size_t)a[d] * q + loc[d]) * c.r1 + b[d]];
-          }
-          if (v == 0.0) continue;
-          ck.v[((size_t)l * Q + merged(loc)) * R1 + rr2] = v;
-        }
-      }
+  // remaining level cores: Kronecker products of axis cores, formed axis by axis as
+  // T <- T (x) c_d over (left rank, local mode, right rank) (axis 0 most significant in each),
+  // then the local modes (loc_0, ..., loc_{D-1}) are merged into the level mode
+  std::vector<int> mq(Q);
+  {
+    std::vector<int> loc(D);
+    for (int lin = 0; lin < Q; ++lin) {
+      int rm = lin;
+      for (int d = D - 1; d >= 0; --d) { loc[d] = rm % q; rm /= q; }
+      mq[lin] = merged(loc);
     }
+  }
+  for (int k = 2; k <= L; ++k) {
+    const HCore& c0 = axes[0].c[k];
+    int A0 = c0.r0, Qm = q, B0 = c0.r1;
+    std::vector<double> T(c0.v);
+    for (int d = 1; d < D; ++d) {
+      const HCore& c = axes[d].c[k];
+      const int A1 = A0 * c.r0, Q1 = Qm * q, B1 = B0 * c.r1;
+      std::vector<double> T1((size_t)A1 * Q1 * B1);
+      for (int a = 0; a < A0; ++a)
+        for (int ad = 0; ad < c.r0; ++ad)
+          for (int l = 0; l < Qm; ++l)
+            for (int ld = 0; ld < q; ++ld) {
+              double* o = &T1[(((size_t)a * c.r0 + ad) * Q1 + (size_t)l * q + ld) * B1];
+              const double* t = &T[((size_t)a * Qm + l) * B0];
+              const double* cc = &c.v[((size_t)ad * q + ld) * c.r1];
+              for (int b = 0; b < B0; ++b)
+                for (int bd = 0; bd < c.r1; ++bd) o[(size_t)b * c.r1 + bd] = t[b] * cc[bd];
+            }
+      T.swap(T1);
+      A0 = A1;
+      Qm = Q1;
+      B0 = B1;
+    }
+    HCore ck{A0, Q, B0, std::vector<double>((size_t)A0 * Q * B0, 0.0)};
+    for (int a = 0; a < A0; ++a)
+      for (int lin = 0; lin < Q; ++lin) {
+        const double* t = &T[((size_t)a * Q + lin) * B0];
+        double* o = &ck.v[((size_t)a * Q + mq[lin]) * B0];
+        for (int b = 0; b < B0; ++b) o[b] = (t[b] == 0.0) ? 0.0 : t[b];
+      }
     out.c.push_back(ck);
   }
   return out;
@@ -569,6 +590,7 @@ HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* s
   lame(mat.E[0], mat.nu, D, g.plane_stress != 0, lam, mu);
   std::vector<HTrain> axes;
   std::vector<AxisOps> cats;
+  std::vector<std::future<AxisOps>> cat_f;
   bool any_clamp = false;
   for (int f = 0; f < 2 * D; ++f) any_clamp |= g.clamped[f] != 0;
   for (int d = 0; d < D; ++d) {
@@ -580,7 +602,12 @@ HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* s
         w[e] = (cx < mat.split_x ? mat.E[0] : mat.E[1]) / mat.E[0];
       }
     }
-    cats.push_back(axis_operators(L, g.lo[d], g.hi[d], w, g.clamped[2 * d] != 0, g.clamped[2 * d + 1] != 0, true));
+    cat_f.push_back(std::async(std::launch::async, [=, &g] {
+      return axis_operators(L, g.lo[d], g.hi[d], w, g.clamped[2 * d] != 0, g.clamped[2 * d + 1] != 0, true);
+    }));
+  }
+  for (auto& f : cat_f) {
+    cats.push_back(f.get());
     axes.push_back(cats.back().joint);
   }
   std::vector<SepTerm> terms = stiffness_terms(D, lam, mu);
@@ -626,9 +653,13 @@ HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* s
 
 HTrain mass_train(const tnfem_grid& g) {
   const int D = g.dim, L = g.levels, n = 1 << L;
-  std::vector<HTrain> axes;
+  std::vector<std::future<AxisOps>> cat_f;
   for (int d = 0; d < D; ++d)
-    axes.push_back(axis_operators(L, g.lo[d], g.hi[d], std::vector<double>(n - 1, 1.0), false, false, false).joint);
+    cat_f.push_back(std::async(std::launch::async, [=, &g] {
+      return axis_operators(L, g.lo[d], g.hi[d], std::vector<double>(n - 1, 1.0), false, false, false);
+    }));
+  std::vector<HTrain> axes;
+  for (auto& f : cat_f) axes.push_back(f.get().joint);
   std::vector<SepTerm> terms;
   for (int c = 0; c < D; ++c) terms.push_back(SepTerm{c, c, 1.0, std::vector<int>(D, OP_M)});
   return combine_axes(axes, terms, D, true);

@@ -139,6 +139,339 @@ __global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A,
   qr_body(m, n, A, Q, R, tau);
 }
 
+// Blocked Householder QR for m >= n (the same reflectors as qr_body, grouped into panels of nb
+// columns in the compact WY form H_p0 ... H_p0+nb-1 = I - V T V^T).  The matrix is transposed into
+// the Q buffer (column-major, W[c][i] = A[i][c], so every column access is coalesced).  Each panel
+// is factorised in shared memory (nb x m), T is formed from tau and V^T V, and the trailing
+// columns take the whole panel at once, A_c <- (I - V T^T V^T) A_c: two passes over each
+// trailing column per panel instead of two per reflector, with nb independent sums in flight.
+// Q = prod_p (I - V_p T_p V_p^T) [I; 0] is accumulated column-major in the A buffer, panels
+// last to first, and transposed into Q.
+constexpr int kQrNbMax = 8;
+constexpr int kQrClMinN = 16;                 // QRs with at least this many columns go to the cluster kernel
+constexpr size_t kQrClSmemMax = 200 * 1024;   // its columns, Q columns and reflector on chip
+constexpr size_t kQrSmemMax = 200 * 1024;  // panel of qr_blk_kernel on chip
+constexpr int QBT = 512;                   // threads of qr_blk_kernel
+
+template <typename T>
+__device__ void qr_blk_load_v(int m, int p0, int pb, const T* __restrict__ W, T* __restrict__ Vs) {
+  // panel columns with the reflector form: zero above the diagonal, unit diagonal, vector below
+  for (long long t = threadIdx.x; t < (long long)pb * m; t += blockDim.x) {
+    const int c = (int)(t / m), i = (int)(t % m);
+    const int j = p0 + c;
+    Vs[t] = (i < j) ? T(0) : (i == j ? T(1) : W[(long long)j * m + i]);
+  }
+}
+
+// T (pb x pb, upper triangular, row-major in Ts) of the panel whose vectors are in Vs.
+template <typename T>
+__device__ void qr_blk_form_t(int m, int p0, int pb, const T* __restrict__ Vs, const T* __restrict__ tau,
+                              T* __restrict__ Ys, T* __restrict__ Ts) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int pr = warp; pr < pb * pb; pr += nw) {
+    const int a = pr / pb, b = pr % pb;
+    if (a >= b) continue;
+    const T* va = Vs + (long long)a * m;
+    const T* vb = Vs + (long long)b * m;
+    T y = T(0);
+    for (int i = p0 + b + lane; i < m; i += 32) y += va[i] * vb[i];
+    y = warp_sum(y);
+    if (lane == 0) Ys[a * kQrNbMax + b] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < pb; ++b) {
+      const T tb = tau[p0 + b];
+      Ts[b * kQrNbMax + b] = tb;
+      for (int a = 0; a < b; ++a) {
+        T acc = T(0);
+        for (int c = a; c < b; ++c) acc += Ts[a * kQrNbMax + c] * Ys[c * kQrNbMax + b];
+        Ts[a * kQrNbMax + b] = -tb * acc;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(QBT) qr_blk_kernel(int m, int n, int nb, T* __restrict__ A, T* __restrict__ Q,
+                                                     T* __restrict__ R, T* __restrict__ tau) {
+  extern __shared__ __align__(16) unsigned char qb_smem[];
+  T* Vs = reinterpret_cast<T*>(qb_smem);  // [nb][m] the current panel
+  __shared__ T sh[33];
+  __shared__ T s_beta, s_tau, s_v0;
+  __shared__ T Ys[kQrNbMax * kQrNbMax], Ts[kQrNbMax * kQrNbMax];
+  const int k = n;  // m >= n
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  T* W = Q;
+  for (long long t = threadIdx.x; t < (long long)m * n; t += blockDim.x) {
+    const int c = (int)(t / m), i = (int)(t % m);
+    W[t] = A[(long long)i * n + c];
+  }
+  __syncthreads();
+  for (int p0 = 0; p0 < k; p0 += nb) {
+    const int pb = min(nb, k - p0);
+    for (long long t = threadIdx.x; t < (long long)pb * m; t += blockDim.x) Vs[t] = W[(long long)p0 * m + t];
+    __syncthreads();
+    // unblocked Householder steps inside the panel
+    for (int jj = 0; jj < pb; ++jj) {
+      const int j = p0 + jj;
+      T* vj = Vs + (long long)jj * m;
+      T part = T(0);
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        const T v = vj[i];
+        part += v * v;
+      }
+      const T tail = block_sum(part, sh);
+      if (threadIdx.x == 0) {
+        const T alpha = vj[j];
+        if (tail == T(0)) {
+          s_tau = T(0);
+          s_beta = alpha;
+          s_v0 = T(1);
+        } else {
+          const T nx = sqrt(alpha * alpha + tail);
+          const T beta = alpha >= T(0) ? -nx : nx;
+          s_tau = (beta - alpha) / beta;
+          s_v0 = alpha - beta;
+          s_beta = beta;
+        }
+        tau[j] = s_tau;
+      }
+      __syncthreads();
+      const T tj = s_tau, v0 = s_v0;
+      if (tj != T(0))
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) vj[i] /= v0;
+      __syncthreads();
+      if (tj != T(0)) {
+        for (int cc = jj + 1 + warp; cc < pb; cc += nw) {
+          T* vc = Vs + (long long)cc * m;
+          T w = (lane == 0) ? vc[j] : T(0);  // the unit entry of v at row j
+          for (int i = j + 1 + lane; i < m; i += 32) w += vj[i] * vc[i];
+          w = warp_sum(w) * tj;
+          if (lane == 0) vc[j] -= w;
+          for (int i = j + 1 + lane; i < m; i += 32) vc[i] -= w * vj[i];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) vj[j] = s_beta;
+      __syncthreads();
+    }
+    // write the factorised panel back (R above and on the diagonal, vectors below)
+    for (long long t = threadIdx.x; t < (long long)pb * m; t += blockDim.x) W[(long long)p0 * m + t] = Vs[t];
+    __syncthreads();
+    if (p0 + pb >= n) break;
+    qr_blk_load_v(m, p0, pb, W, Vs);
+    __syncthreads();
+    qr_blk_form_t(m, p0, pb, Vs, tau, Ys, Ts);
+    // trailing columns: A_c <- A_c - V (T^T (V^T A_c))
+    for (int c = p0 + pb + warp; c < n; c += nw) {
+      T* ac = W + (long long)c * m;
+      T w[kQrNbMax];
+#pragma unroll
+      for (int t = 0; t < kQrNbMax; ++t) w[t] = T(0);
+      for (int i = p0 + lane; i < m; i += 32) {
+        const T a = ac[i];
+#pragma unroll
+        for (int t = 0; t < kQrNbMax; ++t)
+          if (t < pb) w[t] += Vs[(long long)t * m + i] * a;
+      }
+#pragma unroll
+      for (int t = 0; t < kQrNbMax; ++t)
+        if (t < pb) w[t] = warp_sum(w[t]);
+      // w <- T^T w in place (entry b needs w[a] for a <= b: descending b)
+#pragma unroll
+      for (int b = kQrNbMax - 1; b >= 0; --b) {
+        if (b >= pb) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int a = 0; a <= b; ++a) acc += Ts[a * kQrNbMax + b] * w[a];
+        w[b] = acc;
+      }
+      for (int i = p0 + lane; i < m; i += 32) {
+        T sacc = T(0);
+#pragma unroll
+        for (int t = 0; t < kQrNbMax; ++t)
+          if (t < pb) sacc += Vs[(long long)t * m + i] * w[t];
+        ac[i] -= sacc;
+      }
+    }
+    __syncthreads();
+  }
+  for (long long t = threadIdx.x; t < (long long)k * n; t += blockDim.x) {
+    const int i = (int)(t / n), c = (int)(t % n);
+    R[t] = (c >= i) ? W[(long long)c * m + i] : T(0);
+  }
+  // Q = prod_p (I - V_p T_p V_p^T) [I_k; 0], column-major in the A buffer, panels last to first
+  T* QW = A;
+  for (long long t = threadIdx.x; t < (long long)m * k; t += blockDim.x) {
+    const int c = (int)(t / m), i = (int)(t % m);
+    QW[t] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const int np = (k + nb - 1) / nb;
+  for (int pi = np - 1; pi >= 0; --pi) {
+    const int p0 = pi * nb, pb = min(nb, k - p0);
+    qr_blk_load_v(m, p0, pb, W, Vs);
+    __syncthreads();
+    qr_blk_form_t(m, p0, pb, Vs, tau, Ys, Ts);
+    for (int c = p0 + warp; c < k; c += nw) {
+      T* qc = QW + (long long)c * m;
+      T w[kQrNbMax];
+#pragma unroll
+      for (int t = 0; t < kQrNbMax; ++t) w[t] = T(0);
+      for (int i = p0 + lane; i < m; i += 32) {
+        const T a = qc[i];
+#pragma unroll
+        for (int t = 0; t < kQrNbMax; ++t)
+          if (t < pb) w[t] += Vs[(long long)t * m + i] * a;
+      }
+#pragma unroll
+      for (int t = 0; t < kQrNbMax; ++t)
+        if (t < pb) w[t] = warp_sum(w[t]);
+      // w <- T w in place (entry a needs w[b] for b >= a: ascending a)
+#pragma unroll
+      for (int a = 0; a < kQrNbMax; ++a) {
+        if (a >= pb) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int b = a; b < kQrNbMax; ++b)
+          if (b < pb) acc += Ts[a * kQrNbMax + b] * w[b];
+        w[a] = acc;
+      }
+      for (int i = p0 + lane; i < m; i += 32) {
+        T sacc = T(0);
+#pragma unroll
+        for (int t = 0; t < kQrNbMax; ++t)
+          if (t < pb) sacc += Vs[(long long)t * m + i] * w[t];
+        qc[i] -= sacc;
+      }
+    }
+    __syncthreads();
+  }
+  for (long long t = threadIdx.x; t < (long long)m * k; t += blockDim.x) {
+    const int i = (int)(t / k), c = (int)(t % k);
+    Q[t] = QW[(long long)c * m + i];
+  }
+}
+
+// Householder QR (m >= n) on one thread-block cluster.  Binary64 arithmetic runs at a few
+// operations per clock per SM on this part, so a single CTA is bound by its own FP64 pipe (a
+// 1152 x 72 factorisation with its Q is ~12 M FMAs, ~3 ms on one SM).  Here column c lives in the
+// shared memory of CTA c mod C, column-major; at step j the owner of column j forms the reflector
+// (the same arithmetic as qr_body), the cluster barrier publishes it, every CTA copies v_j through
+// distributed shared memory and applies it to its own trailing columns.  Q = H_0 ... H_{n-1} [I; 0]
+// is then accumulated column by column in each owner, reading the final reflectors remotely
+// (no barrier between steps: the factors are read-only by then).
+constexpr int CQT = 256;          // threads per CTA of qr_cluster_kernel
+constexpr int kQrClColMax = 16;   // columns per CTA at most
+
+template <typename T>
+__global__ void __launch_bounds__(CQT) qr_cluster_kernel(int m, int n, const T* __restrict__ A, T* __restrict__ Q,
+                                                         T* __restrict__ R) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cluster = cgr::this_cluster();
+  extern __shared__ __align__(16) unsigned char qc_smem[];
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int ncol = (n + C - 1) / C;
+  T* Wl = reinterpret_cast<T*>(qc_smem);  // [ncol][m] own columns: factors (R above, v below)
+  T* QWl = Wl + (size_t)ncol * m;         // [ncol][m] own columns of Q
+  T* sv = QWl + (size_t)ncol * m;         // [m] the reflector of the current step
+  __shared__ T taul[kQrClColMax];
+  __shared__ T sh[33];
+  __shared__ T s_beta, s_v0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nown = (n - rank + C - 1) / C;  // columns rank, rank + C, ... below n
+  for (int lc = 0; lc < nown; ++lc) {
+    const int c = lc * C + rank;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Wl[(size_t)lc * m + i] = A[(size_t)i * n + c];
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int o = j % C, lj = j / C;
+    if (rank == o) {
+      T* wj = Wl + (size_t)lj * m;
+      T part = T(0);
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        const T v = wj[i];
+        part += v * v;
+      }
+      const T tail = block_sum(part, sh);
+      if (threadIdx.x == 0) {
+        const T alpha = wj[j];
+        if (tail == T(0)) {
+          taul[lj] = T(0);
+          s_beta = alpha;
+          s_v0 = T(1);
+        } else {
+          const T nx = sqrt(alpha * alpha + tail);
+          const T beta = alpha >= T(0) ? -nx : nx;
+          taul[lj] = (beta - alpha) / beta;
+          s_v0 = alpha - beta;
+          s_beta = beta;
+        }
+      }
+      __syncthreads();
+      const T v0 = s_v0;
+      if (taul[lj] != T(0))
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) wj[i] /= v0;
+      if (threadIdx.x == 0) wj[j] = s_beta;
+    }
+    cluster.sync();
+    const T tj = *cluster.map_shared_rank(taul + lj, o);
+    if (tj != T(0)) {
+      const T* wo = cluster.map_shared_rank(Wl, o) + (size_t)lj * m;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) sv[i] = wo[i];
+      __syncthreads();
+      for (int lc = (j + 1 - rank + C - 1) / C + warp; lc < nown; lc += nw) {
+        T* wc = Wl + (size_t)lc * m;
+        T w = (lane == 0) ? wc[j] : T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) w += sv[i] * wc[i];
+        w = warp_sum(w) * tj;
+        if (lane == 0) wc[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) wc[i] -= w * sv[i];
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  // R rows 0..n-1 of the own columns
+  for (int lc = 0; lc < nown; ++lc) {
+    const int c = lc * C + rank;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) R[(size_t)i * n + c] = (i <= c) ? Wl[(size_t)lc * m + i] : T(0);
+  }
+  // Q columns owned here: H_0 ... H_{n-1} e_c, reflectors applied last to first
+  for (int lc = 0; lc < nown; ++lc) {
+    const int c = lc * C + rank;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) QWl[(size_t)lc * m + i] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    const int o = j % C, lj = j / C;
+    const T tj = *cluster.map_shared_rank(taul + lj, o);
+    if (tj == T(0)) continue;
+    const T* wo = cluster.map_shared_rank(Wl, o) + (size_t)lj * m;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) sv[i] = wo[i];
+    __syncthreads();
+    // columns c >= j (columns below j are still e_c, which H_j leaves unchanged)
+    for (int lc = (j - rank + C - 1) / C + warp; lc < nown; lc += nw) {
+      T* qc = QWl + (size_t)lc * m;
+      T w = (lane == 0) ? qc[j] : T(0);
+      for (int i = j + 1 + lane; i < m; i += 32) w += sv[i] * qc[i];
+      w = warp_sum(w) * tj;
+      if (lane == 0) qc[j] -= w;
+      for (int i = j + 1 + lane; i < m; i += 32) qc[i] -= w * sv[i];
+    }
+    __syncthreads();
+  }
+  for (int lc = 0; lc < nown; ++lc) {
+    const int c = lc * C + rank;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Q[(size_t)i * n + c] = QWl[(size_t)lc * m + i];
+  }
+  cluster.sync();  // no CTA leaves while another may still read its reflectors
+}
+
 // Jacobi rotation (cs, sn) annihilating the off-diagonal c of the column-pair Gram block
 // [[a, c], [c, b]]: t = tan(theta) is the smaller root of c t^2 + (b - a) t - c = 0,
 // t = 2c / (d + sign(d) sqrt(d^2 + 4c^2)) with d = b - a, evaluated in binary32 on power-of-two
@@ -693,12 +1026,69 @@ __global__ void __launch_bounds__(CT) qr_ext_coop_kernel(int m, int rk, int w, T
 size_t qr_work_elems(int m, int n) { return (size_t)std::min(m, n) + 8; }
 size_t svd_work_elems(int m, int n) { return (size_t)m * n + (size_t)n * n + (size_t)n + 8; }
 
+// QR on one cluster (qr_cluster_kernel); false when the shape or the device does not allow it.
+template <typename T>
+static bool qr_cluster(tnfem_ctx* ctx, int m, int n, const T* A, T* Q, T* R) {
+  if (m < n || n < kQrClMinN) return false;
+  const int C = std::min(16, (n + 3) / 4);
+  const int ncol = (n + C - 1) / C;
+  if (C < 2 || ncol > kQrClColMax) return false;
+  const size_t smem = ((size_t)2 * ncol + 1) * m * sizeof(T);
+  if (smem > kQrClSmemMax) return false;
+  static unsigned long long attr_set = 0;  // one bit per device
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (!(attr_set & bit)) {
+    if (cudaFuncSetAttribute(qr_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(qr_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrClSmemMax) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr_set |= bit;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(CQT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, qr_cluster_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, m, n, (const T*)A, Q, R) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 template <typename T>
 void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
   if (m <= 0 || n <= 0) return;
   const int k = std::min(m, n);
   ProfScope ps(ctx, TNFEM_PROF_QR, 4.0 * m * n * (double)k, (double)(2 * m * n + m * k + k * n) * sizeof(T));
-  qr_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, Q, R, work);
+  if (qr_cluster<T>(ctx, m, n, A, Q, R)) {
+    count_launch(ctx);
+    check_launch(ctx, "qr");
+    return;
+  }
+  const int nb = (int)std::min<size_t>(kQrNbMax, kQrSmemMax / ((size_t)m * sizeof(T)));
+  if (m >= n && nb >= 1) {
+    const size_t smem = (size_t)nb * m * sizeof(T);
+    if (smem > 48 * 1024)
+      TN_CHECK_CUDA(cudaFuncSetAttribute(qr_blk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    qr_blk_kernel<T><<<1, QBT, smem, ctx->stream>>>(m, n, nb, A, Q, R, work);
+  } else {
+    qr_kernel<T><<<1, LT, 0, ctx->stream>>>(m, n, A, Q, R, work);
+  }
   count_launch(ctx);
   check_launch(ctx, "qr");
 }

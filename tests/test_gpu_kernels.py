@@ -69,7 +69,10 @@ def test_env_left(ctx, ry0, ry1, rx0, rx1, n, a0, a1):
     assert np.all(np.abs(got - ref) <= RTOL * scale)
 
 
-@pytest.mark.parametrize("m,n", [(1, 1), (7, 3), (3, 7), (272, 68), (64, 64), (1056, 136)])
+# m >= n runs the coalesced column-major kernel while m binary64 words fit its 128 KB of shared
+# memory (16384 rows); (16385, 4) and the wide shapes take the row-major kernel.
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 3), (3, 7), (272, 68), (64, 64), (1056, 136), (1152, 72),
+                                 (4608, 53), (16384, 4), (16385, 4), (40, 100)])
 def test_qr(ctx, m, n):
     A = W.random_matrix(9, m, n)
     k = min(m, n)
@@ -86,6 +89,24 @@ def test_qr(ctx, m, n):
     Rn = np.linalg.qr(A)[1][:k]
     sgn = np.sign(np.diag(Rh)) * np.sign(np.diag(Rn))
     np.testing.assert_allclose(sgn[:, None] * Rh, Rn, atol=1e-12 * np.abs(A).max() * max(m, n))
+
+
+@pytest.mark.parametrize("m,n", [(300, 40), (1152, 72), (30, 30)])
+def test_qr_rank_deficient(ctx, m, n):
+    """Columns that repeat earlier ones, a zero column and a zero first column: Q keeps orthonormal
+    columns and Q R reproduces A (the Householder steps with a vanishing tail take tau = 0)."""
+    B = W.random_matrix(4, m, n // 2)
+    A = np.concatenate([B, B[:, : n - n // 2]], axis=1)
+    A[:, 0] = 0.0
+    A[:, n // 3] = 0.0
+    Q = torch.zeros(m * n, dtype=torch.float64, device="cuda")
+    R = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    ctx.op_qr(m, n, dev(A).data_ptr(), Q.data_ptr(), R.data_ptr())
+    Qh = Q.cpu().numpy().reshape(m, n)
+    Rh = R.cpu().numpy().reshape(n, n)
+    assert np.abs(Qh @ Rh - A).max() <= 1e-13 * np.abs(A).max() * m
+    assert np.abs(Qh.T @ Qh - np.eye(n)).max() <= 1e-13 * m
+    assert np.abs(np.tril(Rh, -1)).max() == 0.0
 
 
 # binary64 GEMM engines: 0 binary64 FMA, 1 double-binary32 (hi/lo binary32 pairs; the
@@ -177,9 +198,10 @@ def test_qr_ext(ctx, m, rk, w, kind):
 
 
 # (1, 1), (9, 4): one CTA; (196, 49), (100, 16), (64, 63), (300, 33), (49, 49): one thread-block
-# cluster (16 <= n <= 64); (272, 68), (68, 68), (512, 128): the cooperative multi-CTA kernel
+# cluster (16 <= n <= 64); (272, 68), (68, 68), (512, 128), (848, 72): the cooperative multi-CTA
+# kernel; (5200, 40): columns too long for the cluster's shared memory, the cooperative kernel
 @pytest.mark.parametrize("m,n", [(1, 1), (9, 4), (196, 49), (100, 16), (64, 63), (300, 33), (49, 49),
-                                 (272, 68), (68, 68), (512, 128)])
+                                 (272, 68), (68, 68), (512, 128), (848, 72), (5200, 40)])
 def test_svd(ctx, m, n):
     r = W.rng(11)
     # graded singular values down to 1e-12 to exercise the truncation range
