@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(LT) qr_kernel(int m, int n, T* __restrict__ A,
 // Q = prod_p (I - V_p T_p V_p^T) [I; 0] is accumulated column-major in the A buffer, panels
 // last to first, and transposed into Q.
 constexpr int kQrNbMax = 8;
+constexpr size_t kQrBlkMinElems = 32768;      // smaller matrices stay on qr_kernel
 constexpr int kQrClMinN = 16;                 // QRs with at least this many columns go to the cluster kernel
 constexpr size_t kQrClSmemMax = 200 * 1024;   // its columns, Q columns and reflector on chip
 constexpr size_t kQrSmemMax = 200 * 1024;  // panel of qr_blk_kernel on chip
@@ -355,7 +356,8 @@ __global__ void __launch_bounds__(QBT) qr_blk_kernel(int m, int n, int nb, T* __
   }
 }
 
-// Householder QR (m >= n) on one thread-block cluster.  Binary64 arithmetic runs at a few
+// Householder QR (m >= n) on one thread-block cluster, with qr_kernel's arithmetic in qr_kernel's
+// order (column norm, dot products, updates), so its factors equal qr_kernel's bit for bit.  Binary64 arithmetic runs at a few
 // operations per clock per SM on this part, so a single CTA is bound by its own FP64 pipe (a
 // 1152 x 72 factorisation with its Q is ~12 M FMAs, ~3 ms on one SM).  Here column c lives in the
 // shared memory of CTA c mod C, column-major; at step j the owner of column j forms the reflector
@@ -392,12 +394,25 @@ __global__ void __launch_bounds__(CQT) qr_cluster_kernel(int m, int n, const T* 
     const int o = j % C, lj = j / C;
     if (rank == o) {
       T* wj = Wl + (size_t)lj * m;
-      T part = T(0);
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-        const T v = wj[i];
-        part += v * v;
+      // the column norm in qr_kernel's order (LT threads striding the column, a shuffle tree per
+      // warp, then over the warps), so that both kernels produce the same bits
+      for (int vw = warp; vw < LT / 32; vw += nw) {
+        T part = T(0);
+        for (int i = j + 1 + vw * 32 + lane; i < m; i += LT) {
+          const T v = wj[i];
+          part += v * v;
+        }
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+        if (lane == 0) sh[vw] = part;
       }
-      const T tail = block_sum(part, sh);
+      __syncthreads();
+      if (warp == 0) {
+        T v = sh[lane];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[32] = v;
+      }
+      __syncthreads();
+      const T tail = sh[32];
       if (threadIdx.x == 0) {
         const T alpha = wj[j];
         if (tail == T(0)) {
@@ -426,11 +441,10 @@ __global__ void __launch_bounds__(CQT) qr_cluster_kernel(int m, int n, const T* 
       __syncthreads();
       for (int lc = (j + 1 - rank + C - 1) / C + warp; lc < nown; lc += nw) {
         T* wc = Wl + (size_t)lc * m;
-        T w = (lane == 0) ? wc[j] : T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) w += sv[i] * wc[i];
+        T w = T(0);
+        for (int i = j + lane; i < m; i += 32) w += ((i == j) ? T(1) : sv[i]) * wc[i];
         w = warp_sum(w) * tj;
-        if (lane == 0) wc[j] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) wc[i] -= w * sv[i];
+        for (int i = j + lane; i < m; i += 32) wc[i] -= w * ((i == j) ? T(1) : sv[i]);
       }
     }
     __syncthreads();
@@ -457,11 +471,10 @@ __global__ void __launch_bounds__(CQT) qr_cluster_kernel(int m, int n, const T* 
     // columns c >= j (columns below j are still e_c, which H_j leaves unchanged)
     for (int lc = (j - rank + C - 1) / C + warp; lc < nown; lc += nw) {
       T* qc = QWl + (size_t)lc * m;
-      T w = (lane == 0) ? qc[j] : T(0);
-      for (int i = j + 1 + lane; i < m; i += 32) w += sv[i] * qc[i];
+      T w = T(0);
+      for (int i = j + lane; i < m; i += 32) w += ((i == j) ? T(1) : sv[i]) * qc[i];
       w = warp_sum(w) * tj;
-      if (lane == 0) qc[j] -= w;
-      for (int i = j + 1 + lane; i < m; i += 32) qc[i] -= w * sv[i];
+      for (int i = j + lane; i < m; i += 32) qc[i] -= w * ((i == j) ? T(1) : sv[i]);
     }
     __syncthreads();
   }
@@ -1081,7 +1094,7 @@ void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
     return;
   }
   const int nb = (int)std::min<size_t>(kQrNbMax, kQrSmemMax / ((size_t)m * sizeof(T)));
-  if (m >= n && nb >= 1) {
+  if (m >= n && nb >= 1 && (size_t)m * n >= kQrBlkMinElems) {
     const size_t smem = (size_t)nb * m * sizeof(T);
     if (smem > 48 * 1024)
       TN_CHECK_CUDA(cudaFuncSetAttribute(qr_blk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -69,8 +69,9 @@ def test_env_left(ctx, ry0, ry1, rx0, rx1, n, a0, a1):
     assert np.all(np.abs(got - ref) <= RTOL * scale)
 
 
-# m >= n runs the coalesced column-major kernel while m binary64 words fit its 128 KB of shared
-# memory (16384 rows); (16385, 4) and the wide shapes take the row-major kernel.
+# Paths: n >= 16 with the columns in a cluster's shared memory -> qr_cluster_kernel ((272, 68),
+# (64, 64), (1056, 136), (1152, 72)); larger tall matrices -> the blocked one-CTA kernel ((4608, 53),
+# (16384, 4), (16385, 4)); small or wide ones -> the row-major one-CTA kernel.
 @pytest.mark.parametrize("m,n", [(1, 1), (7, 3), (3, 7), (272, 68), (64, 64), (1056, 136), (1152, 72),
                                  (4608, 53), (16384, 4), (16385, 4), (40, 100)])
 def test_qr(ctx, m, n):
