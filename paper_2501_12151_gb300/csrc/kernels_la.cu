@@ -1,8 +1,12 @@
 // Dense factorizations used by the sweep's orthogonalisation and truncation steps:
 // Householder QR (the reduced QR of Section 4, Eq. qr) and the one-sided Jacobi (Hestenes)
-// SVD used for TT truncation.  One CTA of 1024 threads works on a matrix held in global
-// memory (L2/L1-resident at these sizes); all loops have fixed trip counts, nothing waits on
-// another block.
+// SVD used for TT truncation.  Binary64 runs at ~2 FMAs per clock per SM on this part, so the
+// larger factorizations are spread over SMs: a thread-block cluster with the columns in
+// distributed shared memory (qr_cluster_kernel, svd_cluster_kernel) or a cooperative grid with a
+// bounded grid barrier (svd_coop_kernel, qr_ext_coop_kernel); small ones run on one CTA
+// (qr_kernel, qr_blk_kernel, svd_kernel).  Cluster and CTA barriers are hardware barriers that
+// every thread reaches the same number of times; the grid barriers give up after a bounded wait
+// and report it.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
