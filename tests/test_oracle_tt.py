@@ -162,3 +162,93 @@ def test_local_system_is_projection():
     Ad = tt.mpo_full(A)
     np.testing.assert_allclose(B, V.T @ Ad @ V, atol=1e-12 * np.abs(Ad).max())
     assert np.allclose(V.T @ V, np.eye(V.shape[1]), atol=1e-12)
+
+
+def _interface_basis(x):
+    """V with V[:, c] = the full vector of the three-core train whose middle core is unit vector c."""
+    r0, n, r1 = x[1].shape
+    N = int(np.prod([c.shape[1] for c in x]))
+    V = np.zeros((N, r0 * n * r1))
+    for col in range(r0 * n * r1):
+        e = np.zeros(r0 * n * r1)
+        e[col] = 1.0
+        V[:, col] = tt.tt_full([x[0], e.reshape(r0, n, r1), x[2]])
+    return V
+
+
+def _three_core_setup(seed):
+    pr = W.steel_plate_2d(levels=2)
+    A, _ = mpo.stiffness_mpo(pr.grid, pr.material)
+    x = tt.orthogonalize_right(W.random_tt(seed, [2, 4, 4], [1, 2, 3, 1]))
+    x = tt.orthogonalize_left(x, upto=1)
+    return A, x
+
+
+def test_local_matvec_is_projected_operator():
+    """The structured local matvec (the contraction order the GPU kernels follow) applied to a
+    core c equals V^T A V c with V the interface basis and A the full operator matrix."""
+    A, x = _three_core_setup(3)
+    PhiL = amen.env_left_op(np.ones((1, 1, 1)), x[0], A[0], x[0])
+    PhiR = amen.env_right_op(np.ones((1, 1, 1)), x[2], A[2], x[2])
+    V = _interface_basis(x)
+    Ad = tt.mpo_full(A)
+    c = W.rng(4).standard_normal(x[1].shape)
+    got = amen.local_matvec(PhiL, A[1], PhiR, c).ravel()
+    np.testing.assert_allclose(got, V.T @ (Ad @ (V @ c.ravel())), atol=1e-12 * np.abs(Ad).max() * np.abs(c).max())
+
+
+def test_local_rhs_is_projected_load():
+    """The local right-hand side from the load environments equals V^T f."""
+    A, x = _three_core_setup(5)
+    f = W.random_tt(6, [2, 4, 4], [1, 2, 2, 1])
+    PsiL = amen.env_left_vec(np.ones((1, 1)), x[0], f[0])
+    PsiR = amen.env_right_vec(np.ones((1, 1)), x[2], f[2])
+    g = amen.local_rhs(PsiL, f[1], PsiR).ravel()
+    np.testing.assert_allclose(g, _interface_basis(x).T @ tt.tt_full(f), atol=1e-12)
+
+
+def test_environments_contract_to_bilinear_forms():
+    """Sweeping the operator environments across two different trains y, x from either end gives
+    y^T A x of the full matrix; the load environments give y^T f.  A is a random non-symmetric
+    operator train, so that exchanging y and x (or the row and column index of A) is detected."""
+    r = W.rng(12)
+    modes = [2, 4, 4]
+    a = [1, 3, 2, 1]
+    A = [r.standard_normal((a[k], modes[k], modes[k], a[k + 1])) for k in range(3)]
+    y = W.random_tt(7, modes, [1, 2, 3, 1])
+    x = W.random_tt(8, modes, [1, 3, 2, 1])
+    f = W.random_tt(9, modes, [1, 2, 2, 1])
+    want = tt.tt_full(y) @ tt.mpo_full(A) @ tt.tt_full(x)
+    Phi = np.ones((1, 1, 1))
+    for k in range(len(A)):
+        Phi = amen.env_left_op(Phi, y[k], A[k], x[k])
+    assert Phi.shape == (1, 1, 1) and Phi[0, 0, 0] == pytest.approx(want, rel=1e-12)
+    Phi = np.ones((1, 1, 1))
+    for k in reversed(range(len(A))):
+        Phi = amen.env_right_op(Phi, y[k], A[k], x[k])
+    assert Phi[0, 0, 0] == pytest.approx(want, rel=1e-12)
+    wantf = tt.tt_full(y) @ tt.tt_full(f)
+    Psi = np.ones((1, 1))
+    for k in range(len(f)):
+        Psi = amen.env_left_vec(Psi, y[k], f[k])
+    assert Psi[0, 0] == pytest.approx(wantf, rel=1e-12)
+    Psi = np.ones((1, 1))
+    for k in reversed(range(len(f))):
+        Psi = amen.env_right_vec(Psi, y[k], f[k])
+    assert Psi[0, 0] == pytest.approx(wantf, rel=1e-12)
+
+
+def test_cg_solves_spd_system():
+    """Plain CG on a random SPD matrix stops at the requested residual and approaches the direct
+    solution; a zero right-hand side returns at once."""
+    r = W.rng(10)
+    M = r.standard_normal((40, 40))
+    B = M @ M.T + 40 * np.eye(40)
+    g = r.standard_normal(40)
+    x, it = amen.cg(lambda v: B @ v, g, np.zeros(40), 1e-12, 500)
+    assert 0 < it < 500
+    # the recursive residual met 1e-12; the true one differs from it by rounding only
+    assert np.linalg.norm(g - B @ x) <= 2e-12 * np.linalg.norm(g)
+    np.testing.assert_allclose(x, np.linalg.solve(B, g), rtol=1e-9)
+    z, it0 = amen.cg(lambda v: B @ v, np.zeros(40), np.ones(40), 1e-12, 500)
+    assert it0 == 0 and not z.any()
