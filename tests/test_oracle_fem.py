@@ -194,3 +194,31 @@ def test_cantilever_tip_deflection_section6():
     # Q1 elements are too stiff in bending on 20:1 elements; refinement approaches the formula
     assert defl[1] > defl[0]
     assert abs(defl[1] - ref) / ref < 0.05, (defl, ref)
+
+
+@pytest.mark.parametrize("dim,levels", [(2, 3), (3, 2)])
+def test_load_resultants_equal_applied_forces(dim, levels):
+    """Before boundary conditions the nodal load vector's components sum to the applied resultant:
+    rho g |Omega| downward for gravity (the mass matrix integrates constants exactly) and t_c |F|
+    for a uniform traction on face F.  A wrong mass scaling, a traction on the wrong face or
+    component, or a dropped sign fails it."""
+    g = W.Grid(dim=dim, levels=levels, lo=(0.0, 0.0, 0.0), hi=(2.0, 0.5, 0.25))
+    m = W.Material()
+    ext = [g.hi[d] - g.lo[d] for d in range(dim)]
+    vol = float(np.prod(ext))
+    N = g.n ** dim
+    f = fem.load_vector(g, m, [W.Load(kind="gravity", rho=7850.0)])
+    res = [f[c * N:(c + 1) * N].sum() for c in range(dim)]
+    np.testing.assert_allclose(res[:-1], 0.0, atol=1e-9 * 7850.0 * W.GRAVITY * vol)
+    assert res[-1] == pytest.approx(-7850.0 * W.GRAVITY * vol, rel=1e-12)
+    for face in range(2 * dim):
+        t = (3.0, -5.0, 7.0)[:dim] + (0.0,) * (3 - dim)
+        f = fem.load_vector(g, m, [W.Load(kind="traction", face=face, traction=t)])
+        area = vol / ext[face // 2]
+        res = [f[c * N:(c + 1) * N].sum() for c in range(dim)]
+        np.testing.assert_allclose(res, [t[c] * area for c in range(dim)], rtol=1e-12)
+        # only the nodes of that face carry it
+        coord = np.indices((g.n,) * dim).reshape(dim, -1)[face // 2]
+        on_face = coord == (g.n - 1 if face % 2 else 0)
+        for c in range(dim):
+            assert not f[c * N:(c + 1) * N][~on_face].any()
