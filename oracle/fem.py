@@ -421,9 +421,121 @@ def energy_norm(A: sp.csr_matrix, v: np.ndarray) -> float:
     return float(math.sqrt(max(v @ (A @ v), 0.0)))
 
 
-def energy(A: sp.csr_matrix, u: np.ndarray) -> float:
-    """Strain energy 1/2 u^T A u."""
-    return 0.5 * float(u @ (A @ u))
+# ---------------------------------------------------------------------------------------
+# u_h at large sizes: conjugate gradients preconditioned by a geometric multigrid V-cycle
+# ---------------------------------------------------------------------------------------
+#
+# The result is still the definition above, u_h = A^{-1} f (Section 3, Eq. femsys); the
+# V-cycle only changes how fast CG gets there.  It is a textbook construction: linear
+# interpolation between uniform grids of 2^l and 2^(l-1) nodes per axis (the grids are not
+# nested: an odd number of intervals cannot be halved), Galerkin coarse operators P^T A P,
+# Chebyshev smoothing on D^{-1} A (the same polynomial before and after the coarse correction,
+# so the cycle is a symmetric operator), a sparse direct solve on the coarsest grid.
+
+def interpolation_1d(n_fine: int, n_coarse: int) -> sp.csr_matrix:
+    """Linear interpolation from n_coarse to n_fine equidistant nodes of the same interval."""
+    t = np.arange(n_fine) * (n_coarse - 1) / (n_fine - 1)   # fine nodes in coarse index units
+    j = np.minimum(np.floor(t).astype(np.int64), n_coarse - 2)
+    w = t - j
+    rows = np.concatenate([np.arange(n_fine), np.arange(n_fine)])
+    cols = np.concatenate([j, j + 1])
+    vals = np.concatenate([1.0 - w, w])
+    P = sp.csr_matrix((vals, (rows, cols)), shape=(n_fine, n_coarse))
+    P.eliminate_zeros()
+    return P
+
+
+def vector_interpolation(dim: int, n_fine: int, n_coarse: int) -> sp.csr_matrix:
+    """I_D (x) P_1D (x) ... (x) P_1D in the natural ordering (component, then x, y[, z])."""
+    P1 = interpolation_1d(n_fine, n_coarse)
+    P = P1
+    for _ in range(dim - 1):
+        P = sp.kron(P, P1, format="csr")
+    return sp.kron(sp.identity(dim, format="csr"), P, format="csr")
+
+
+class MultigridV:
+    """Symmetric V-cycle for the BC-applied elasticity matrix on a 2^levels tensor grid."""
+
+    def __init__(self, dim: int, levels: int, A: sp.csr_matrix, coarsest_levels: int = 4, degree: int = 3):
+        self.degree = degree
+        self.As, self.Ps, self.dinv, self.lmax = [A.tocsr()], [], [], []
+        l = levels
+        while l > coarsest_levels:
+            P = vector_interpolation(dim, 1 << l, 1 << (l - 1))
+            self.Ps.append(P)
+            self.As.append((P.T @ self.As[-1] @ P).tocsr())
+            l -= 1
+        for Al in self.As[:-1]:
+            d = 1.0 / Al.diagonal()
+            self.dinv.append(d)
+            self.lmax.append(1.1 * self._power_max(Al, d))
+        self.coarse = spla.splu(self.As[-1].tocsc())
+
+    @staticmethod
+    def _power_max(A, dinv, iters: int = 30) -> float:
+        """Largest eigenvalue of D^{-1} A by power iteration (seeded start)."""
+        v = np.random.Generator(np.random.Philox(key=17)).standard_normal(A.shape[0])
+        lam = 0.0
+        for _ in range(iters):
+            w = dinv * (A @ v)
+            lam = float(np.linalg.norm(w) / np.linalg.norm(v))
+            v = w / np.linalg.norm(w)
+        return lam
+
+    def _smooth(self, l: int, x: np.ndarray, b: np.ndarray) -> np.ndarray:
+        """Chebyshev iteration of the given degree on D^{-1} A over [lmax/30, lmax]."""
+        A, dinv, hi = self.As[l], self.dinv[l], self.lmax[l]
+        lo = hi / 30.0
+        theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        r = dinv * (b - A @ x)
+        d = r / theta
+        for _ in range(self.degree):
+            x = x + d
+            r = r - dinv * (A @ d)
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            d = rho_new * rho * d + 2.0 * rho_new / delta * r
+            rho = rho_new
+        return x
+
+    def cycle(self, b: np.ndarray, l: int = 0) -> np.ndarray:
+        if l == len(self.As) - 1:
+            return self.coarse.solve(b)
+        A, P = self.As[l], self.Ps[l]
+        x = self._smooth(l, np.zeros_like(b), b)
+        x = x + P @ self.cycle(P.T @ (b - A @ x), l + 1)
+        return self._smooth(l, x, b)
+
+
+def solve_mg(grid: Grid, A: sp.csr_matrix, f: np.ndarray, rtol: float = 1e-14, maxit: int = 500):
+    """u_h = A^{-1} f by V-cycle preconditioned CG, for grids too large for a direct solve.
+
+    Stops when the preconditioned residual r^T M r has fallen by rtol^2 (the recursive 2-norm
+    residual can stall near eps * cond(A) before the error does).  Returns (u_h, info) with the
+    iteration count and the true relative residual ||f - A u|| / ||f||.
+    """
+    mg = MultigridV(grid.dim, grid.levels, A)
+    x = np.zeros_like(f)
+    r = f.copy()
+    z = mg.cycle(r)
+    p = z.copy()
+    rz = float(r @ z)
+    rz0 = rz
+    it = 0
+    while it < maxit and rz > rtol * rtol * rz0:
+        Ap = A @ p
+        alpha = rz / float(p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        z = mg.cycle(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+    res = float(np.linalg.norm(f - A @ x) / np.linalg.norm(f))
+    return x, {"iters": it, "rel_residual": res, "converged": rz <= rtol * rtol * rz0}
 
 
 def manufactured_errors(grid: Grid, mat: Material, u: np.ndarray):

@@ -176,12 +176,6 @@ def tt_add(x: Cores, y: Cores, beta: float = 1.0) -> Cores:
     return out
 
 
-def tt_scale(x: Cores, alpha: float) -> Cores:
-    out = [c.copy() for c in x]
-    out[0] = out[0] * alpha
-    return out
-
-
 def tt_dot(x: Cores, y: Cores) -> float:
     """<x, y> by left-to-right contraction of the Gram environments."""
     E = np.ones((1, 1))
@@ -200,17 +194,6 @@ def mpo_apply(A: Cores, x: Cores) -> Cores:
         r0, _, r1 = xk.shape
         c = np.einsum("aijb,rjs->aribs", Ak, xk)
         out.append(c.reshape(a0 * r0, n, a1 * r1))
-    return out
-
-
-def mpo_mpo(A: Cores, B: Cores) -> Cores:
-    """Exact product of two TT-operators (A B)."""
-    out = []
-    for Ak, Bk in zip(A, B):
-        a0, n, _, a1 = Ak.shape
-        b0, _, _, b1 = Bk.shape
-        c = np.einsum("aijb,cjkd->acikbd", Ak, Bk).reshape(a0 * b0, n, n, a1 * b1)
-        out.append(c)
     return out
 
 
@@ -301,21 +284,5 @@ def kron_levels(axis_ops: Sequence[Cores]) -> Cores:
             a0, n, m, a1 = c.shape
             b0, p, q, b1 = e.shape
             c = np.einsum("aijb,ckld->acikjlbd", c, e).reshape(a0 * b0, n * p, m * q, a1 * b1)
-        out.append(c)
-    return out
-
-
-def kron_levels_vec(axis_vecs: Sequence[Cores]) -> Cores:
-    """Interleave per-axis 1D QTT vectors into level cores (merged mode, x bit first)."""
-    D = len(axis_vecs)
-    L = len(axis_vecs[0])
-    out = []
-    for k in range(L):
-        c = axis_vecs[0][k]
-        for d in range(1, D):
-            e = axis_vecs[d][k]
-            a0, n, a1 = c.shape
-            b0, p, b1 = e.shape
-            c = np.einsum("aib,cjd->acijbd", c, e).reshape(a0 * b0, n * p, a1 * b1)
         out.append(c)
     return out

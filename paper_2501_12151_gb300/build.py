@@ -45,7 +45,7 @@ def _needs(obj: str, deps) -> bool:
 def build(verbose: bool = False, jobs: int = 0) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "tnfem.h"))
     srcs = sources()
     objs = []

@@ -222,3 +222,87 @@ def test_load_resultants_equal_applied_forces(dim, levels):
         on_face = coord == (g.n - 1 if face % 2 else 0)
         for c in range(dim):
             assert not f[c * N:(c + 1) * N][~on_face].any()
+
+
+def test_fourier_body_force_nodal_values_by_hand():
+    """Fourier body force f_c(x) = scale * sum_m a[c,m] sin(pi k_m . x + phi_m) (the 3D
+    cantilever's seeded load) at nodes chosen so that every sine has a value written by hand.
+
+    Grid: 4 nodes per axis on [0, 1.5]^2, so coordinates are multiples of 1/2.  Two modes with
+    k_0 = (1, 2), phi_0 = pi/6 and k_1 = (3, 1), phi_1 = pi/3; amplitudes a = [[2, -1], [0.5, 4]]
+    (component-major), scale 0.5.  At x = (1/2, 1/2): pi k_0.x = 3pi/2 and pi k_1.x = 2pi, so
+    sin(3pi/2 + pi/6) = -cos(pi/6) and sin(2pi + pi/3) = sin(pi/3).  At x = (1, 0): pi and 3pi,
+    so both sines are -sin(phi_m).  A dropped pi, a transposed amplitude or wave-number index,
+    or a phase added outside the sine fails one of the four values."""
+    g = W.Grid(dim=2, levels=2, lo=(0.0, 0.0, 0.0), hi=(1.5, 1.5, 0.0))
+    amp = np.array([[2.0, -1.0], [0.5, 4.0]])
+    wave = np.array([[1, 2], [3, 1]])
+    phase = np.array([np.pi / 6, np.pi / 3])
+    ld = W.Load(kind="fourier", amp=amp, wave=wave, phase=phase, scale=0.5)
+    f0 = fem.nodal_body_force(g, W.Material(), ld).reshape(2, 4, 4)
+    c6, s3, s6 = math.sqrt(3) / 2, math.sqrt(3) / 2, 0.5   # cos(pi/6), sin(pi/3), sin(pi/6)
+    # node (i, j) = (1, 1) is x = (1/2, 1/2); node (2, 0) is x = (1, 0)
+    assert f0[0, 1, 1] == pytest.approx(0.5 * (2.0 * -c6 + -1.0 * s3), rel=1e-13)
+    assert f0[1, 1, 1] == pytest.approx(0.5 * (0.5 * -c6 + 4.0 * s3), rel=1e-13)
+    assert f0[0, 2, 0] == pytest.approx(0.5 * (2.0 * -s6 + -1.0 * -s3), rel=1e-13)
+    assert f0[1, 2, 0] == pytest.approx(0.5 * (0.5 * -s6 + 4.0 * -s3), rel=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fourier_load_integrates_to_closed_form(dim):
+    """Summed over the nodes, M f0 of one Fourier mode is the integral of the nodal interpolant
+    of f_c, which converges at O(h^2) to the closed-form integral of scale * a_c sin(pi k.x + phi)
+    over the unit square / cube: Im(exp(i phi) prod_d (exp(i pi k_d) - 1) / (i pi k_d))."""
+    k = np.array([1, 3, 1])[:dim]          # odd wave numbers: no factor of the integral vanishes
+    phi = 0.7
+    amp = np.array([[1.5], [-0.8], [2.5]])[:dim]
+    ld = W.Load(kind="fourier", amp=amp, wave=k[None, :], phase=np.array([phi]), scale=3.0)
+    exact_unit = (np.exp(1j * phi) * np.prod([(np.exp(1j * np.pi * kd) - 1) / (1j * np.pi * kd) for kd in k])).imag
+    want = 3.0 * amp[:, 0] * exact_unit
+    sums, hs = [], []
+    for levels in ((5, 6) if dim == 2 else (3, 4)):
+        g = W.Grid(dim=dim, levels=levels)
+        N = g.n ** dim
+        f = fem.load_vector(g, W.Material(), [ld])
+        sums.append(np.array([f[c * N:(c + 1) * N].sum() for c in range(dim)]))
+        hs.append(1.0 / (g.n - 1))
+    errs = [np.abs(s - want).max() / np.abs(want).max() for s in sums]
+    # second order: the error falls with h^2 ...
+    assert errs[1] < 0.3 * errs[0], errs
+    # ... and Richardson extrapolation in h^2 removes it to the next order
+    (sc, sf), (hc, hf) = sums, hs
+    extrap = (sf * hc * hc - sc * hf * hf) / (hc * hc - hf * hf)
+    assert np.abs(extrap - want).max() < 0.05 * errs[1] * np.abs(want).max(), (extrap, want, errs)
+
+
+def test_interpolation_reproduces_linear_fields():
+    """The multigrid prolongation (linear interpolation between grids of 2^l and 2^(l-1) nodes)
+    is exact on affine fields, per axis and for the vector field (rigid rotations included)."""
+    P = fem.interpolation_1d(16, 8)
+    xc, xf = np.linspace(0.0, 1.0, 8), np.linspace(0.0, 1.0, 16)
+    np.testing.assert_allclose(P @ (2.0 - 3.0 * xc), 2.0 - 3.0 * xf, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(P.sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    Pv = fem.vector_interpolation(2, 16, 8)
+    Xc, Yc = np.meshgrid(xc, xc, indexing="ij")
+    Xf, Yf = np.meshgrid(xf, xf, indexing="ij")
+    rot_c = np.concatenate([-Yc.ravel(), Xc.ravel()])
+    rot_f = np.concatenate([-Yf.ravel(), Xf.ravel()])
+    np.testing.assert_allclose(Pv @ rot_c, rot_f, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("problem", ["steel6", "steel7", "cube3"])
+def test_multigrid_cg_matches_direct_solve(problem):
+    """The V-cycle preconditioned CG used for u_h at large sizes reaches the sparse direct
+    solution (the definition u_h = A^{-1} f) on grids small enough for a direct solve.  (Its
+    isotropic coarsening suits square elements; it is not used for the 20:1 cantilever.)"""
+    if problem == "steel6":
+        pr = W.steel_plate_2d(levels=6)
+    elif problem == "steel7":
+        pr = W.steel_plate_2d(levels=7)
+    else:
+        pr = W.cantilever_3d(levels=3)
+    Abc, f = fem.system(pr.grid, pr.material, pr.loads)
+    u, info = fem.solve_mg(pr.grid, Abc, f)
+    ud = spla.spsolve(Abc.tocsc(), f)
+    assert info["converged"] and info["iters"] < 100, info
+    assert fem.energy_norm(Abc, u - ud) <= 1e-10 * fem.energy_norm(Abc, ud)
