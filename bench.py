@@ -488,6 +488,76 @@ def run_reference(args):
     }
 
 
+def run_served(args):
+    """Config-5 serving: the first ``--served`` requests of the seeded stream of 512 (Poisson
+    arrivals at 200/s; per request dimension, levels, E, nu, load and rank cap drawn from its own
+    seed) submitted at their arrival times to the serving loop; solves/s = requests / (last
+    completion - first arrival), latency = submit -> completion.  Next to it, the same requests
+    solved one at a time in binary64 by one context (no overlap)."""
+    import numpy as np
+    import torch
+    from paper_2501_12151_gb300 import tnfem
+    from paper_2501_12151_gb300 import workloads as W
+    arrivals, reqs = W.served_requests(seed=0, n=512, rate=200.0)
+    n = min(args.served, len(reqs))
+    arrivals, reqs = arrivals[:n], reqs[:n]
+    srv = tnfem.Server(0, workers=args.serve_workers, hbm_budget=args.serve_budget)
+    # warm-up (untimed): one small request of each dimension through the same workers
+    for pr in (W.steel_plate_2d(levels=5, rank_cap=16, tol=1e-6, precision="mixed-local"),
+               W.cantilever_3d(levels=3, rank_cap=16, tol=1e-6, precision="mixed-local")):
+        for _ in range(args.serve_workers):
+            srv.wait(srv.submit(pr.grid, pr.material, pr.loads, pr.opts), take=False)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        ids = []
+        for t_arr, pr in zip(arrivals, reqs):
+            dt = t_arr - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(pr.grid, pr.material, pr.loads, pr.opts))
+        res = [srv.wait(i, take=False)[1] for i in ids]
+        t_total = time.perf_counter() - t0
+    srv.stop()
+    lat = sorted(r["latency_us"] * 1e-3 for r in res)
+    ok = sum(r["status"] in ("OK", "NOT_CONVERGED") for r in res)
+    # one at a time, binary64, one context
+    ctx = tnfem.Context(0)
+    seq = []
+    t1 = time.perf_counter()
+    for pr in reqs[: args.serve_fp64]:
+        o = W.SolveOpts(**{**pr.opts.__dict__, "precision": "fp64"})
+        ts = time.perf_counter()
+        A = ctx.stiffness(pr.grid, pr.material)
+        f = ctx.load(pr.grid, pr.material, pr.loads)
+        u, info = ctx.solve(A, f, o)
+        u.cores()
+        seq.append(1e3 * (time.perf_counter() - ts))
+        del A, f, u
+    t_seq = time.perf_counter() - t1
+    dims = [pr.grid.dim for pr in reqs]
+    return {
+        "metric": "served TT solves: solves/s, p50/p99 latency (continuous batching)",
+        "value": n / t_total, "unit": "solves/s", "n_gpus": 1, "steps": n, "warmup": 2 * args.serve_workers,
+        "ms_per_step": 1e3 * t_total / n,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                       "max": lat[-1]},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"served batch: first {n} of 512 seeded requests, Poisson arrivals at 200/s, "
+                               f"2D L 6..10 / 3D L 5..9, E log-uniform 1e9..3e11, nu 0.2..0.45, gravity / traction / "
+                               f"Fourier load, rank cap 16..96, mixed-local tol 1e-6",
+                   "requests": n, "requests_2d": dims.count(2), "requests_3d": dims.count(3),
+                   "workers": args.serve_workers, "parallelism": "one GPU, overlapping worker streams"},
+        "served": {"completed": ok, "makespan_s": t_total,
+                   "mean_run_ms": float(np.mean([r["run_us"] for r in res])) * 1e-3,
+                   "mean_queued_ms": float(np.mean([r["queued_us"] for r in res])) * 1e-3,
+                   "peak_within_estimate": all(r["peak_bytes"] <= r["est_bytes"] for r in res),
+                   "statuses": sorted({r["status"] for r in res})},
+        "one_at_a_time_fp64": {"requests": len(seq), "solves_per_s": len(seq) / t_seq if seq else None,
+                               "p50_ms": sorted(seq)[len(seq) // 2] if seq else None},
+        "clocks": clk.summary(),
+    }
+
+
 def run_kernel_probe(args):
     """A few launches of each local-matvec engine at the solve's working shapes (for ncu): the
     binary32 contraction on CUDA cores and on the tcgen05 tensor cores, and the binary64 one,
@@ -539,14 +609,18 @@ def run_kernel_probe(args):
     for dt, name in ((np.float32, "f32"), (np.float64, "f64")):
         t = [dev(v, dt) for v in (SL, SA, SR, g)]
         walls = []
-        for _ in range(args.probe_reps):
-            xg = torch.zeros(r0 * n * r1, dtype=t[0].dtype, device="cuda")
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            its, _ = ctx.op_local_cg("fp64" if dt == np.float64 else "fp32", 1, r0, n, r1, a0, a1,
-                                     *[v.data_ptr() for v in t], xg.data_ptr(), 0.0, args.probe_cg_steps)
-            torch.cuda.synchronize()
-            walls.append(time.perf_counter() - t0)
+        try:
+            for _ in range(args.probe_reps):
+                xg = torch.zeros(r0 * n * r1, dtype=t[0].dtype, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                its, _ = ctx.op_local_cg("fp64" if dt == np.float64 else "fp32", 1, r0, n, r1, a0, a1,
+                                         *[v.data_ptr() for v in t], xg.data_ptr(), 0.0, args.probe_cg_steps)
+                torch.cuda.synchronize()
+                walls.append(time.perf_counter() - t0)
+        except tnfem.TnfemError as e:  # the fused kernel's shape limits (the sweep then steps per launch)
+            out[f"{name}_fused_cg"] = str(e)
+            continue
         out[f"{name}_fused_cg_steps"] = its
         out[f"{name}_fused_cg_wall_us"] = 1e6 * min(walls)
     return out
@@ -576,8 +650,14 @@ def main(argv=None):
     ap.add_argument("--probe-shape", type=int, nargs=5, default=[49, 4, 49, 51, 51], metavar=("R0", "N", "R1", "A0", "A1"))
     ap.add_argument("--probe-reps", type=int, default=3)
     ap.add_argument("--probe-cg-steps", type=int, default=50, help="steps of the fused CG launch in the probe")
+    ap.add_argument("--served", type=int, default=0, help="run the served batch with this many requests instead")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-budget", type=int, default=0, help="device-memory budget of the server (0: 80%% of free)")
+    ap.add_argument("--serve-fp64", type=int, default=16, help="requests of the one-at-a-time binary64 baseline")
     args = ap.parse_args(argv)
-    if args.kernel_probe:
+    if args.served > 0:
+        out = run_served(args)
+    elif args.kernel_probe:
         out = run_kernel_probe(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -38,9 +38,14 @@ typedef enum {
   TNFEM_E_NOMEM = 2,          /* device or host allocation failed */
   TNFEM_E_CUDA = 3,           /* a CUDA runtime call failed (message holds the CUDA error) */
   TNFEM_E_NOT_CONVERGED = 4,  /* solve stopped at max_sweeps / max_refine; result still filled */
-  TNFEM_E_TIMEOUT = 5,        /* a bounded device-side wait ran out */
-  TNFEM_E_BUDGET = 6,         /* request exceeds the context's device-memory budget */
-  TNFEM_E_NUMERIC = 7         /* NaN/Inf or a breakdown (non-positive curvature) was detected */
+  TNFEM_E_TIMEOUT = 5,        /* a bounded device-side wait ran out, or a solve's timeout_us passed
+                                 (then the solve's result is still filled) */
+  TNFEM_E_BUDGET = 6,         /* an allocation would exceed the context's device-memory budget
+                                 (tnfem_set_hbm_budget); the context stays usable */
+  TNFEM_E_NUMERIC = 7         /* NaN/Inf detected: every core step of the sweep checks its local
+                                 right-hand side, residual and solution, so a non-finite value in
+                                 the operator, the load, the start or an environment ends the solve
+                                 within one sweep (no result is returned) */
 } tnfem_status;
 
 typedef struct tnfem_ctx tnfem_ctx;
@@ -84,11 +89,16 @@ typedef struct {
 
 /* FP64: every step in binary64.
  * MIXED: binary32 AMEn solves of the correction equation A e = f - A u inside an outer iterative
- *   refinement whose residual projections and u + e rounding are binary64.
+ *   refinement whose residual projections and u + e rounding are binary64.  The refinement
+ *   contracts only while cond(A) times the binary32 unit roundoff is well below 1: it converges
+ *   on small grids and stalls near 4e-4 relative energy error on 2^10 x 2^10 nodes.
  * MIXED_LOCAL: binary64 sweep (environments, projections, QR, SVD) whose local systems are solved
  *   by binary32 preconditioned CG, refined against the binary64 local residual until it meets the
- *   same tolerance as FP64. */
-typedef enum { TNFEM_FP64 = 0, TNFEM_MIXED = 1, TNFEM_MIXED_LOCAL = 2 } tnfem_precision;
+ *   same tolerance as FP64.
+ * MIXED_TF32: MIXED_LOCAL with the binary32 local matvecs on the tcgen05 tensor cores (TF32
+ *   products in the three-term split a b = a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation);
+ *   the same as MIXED_LOCAL with tensor_cores = 1. */
+typedef enum { TNFEM_FP64 = 0, TNFEM_MIXED = 1, TNFEM_MIXED_LOCAL = 2, TNFEM_MIXED_TF32 = 3 } tnfem_precision;
 
 typedef struct {
   double tol;          /* sweep stop: largest local residual or local update <= tol; truncation
@@ -109,6 +119,9 @@ typedef struct {
                           field is negative */
   int cg_engine;       /* local solves: 0 one persistent cooperative kernel per solve (default),
                           1 one launch per conjugate-gradient step (graph-replayed chunks) */
+  int64_t timeout_us;  /* wall-clock limit of the solve in microseconds (0: none), checked after
+                          every core step; on expiry the solve returns TNFEM_E_TIMEOUT with *u and
+                          *info filled from the last completed core step */
 } tnfem_solve_opts;
 
 typedef struct {
@@ -146,6 +159,16 @@ const char* tnfem_last_error(const tnfem_ctx* ctx);
 tnfem_status tnfem_set_stream(tnfem_ctx* ctx, void* stream);
 /* Number of kernels this context has launched since creation (for accounting). */
 long long tnfem_kernel_launches(const tnfem_ctx* ctx);
+/* Device-memory budget of the context in bytes (0: none, the default).  Every device allocation
+ * of the context (its own cudaMalloc or the allocator callback) is counted; one that would take
+ * the bytes held above the budget fails with TNFEM_E_BUDGET, the call that needed it returns that
+ * status and frees what it had taken, and the context stays usable.  Bytes already held are not
+ * affected by a lower budget.  The serving loop admits requests against this figure. */
+tnfem_status tnfem_set_hbm_budget(tnfem_ctx* ctx, size_t bytes);
+/* Bytes of device memory the context holds now (in_use) and its high-water mark since creation or
+ * the last reset (peak); reset_peak != 0 sets the mark to the current holding.  Either output
+ * pointer may be NULL. */
+tnfem_status tnfem_memory_stats(tnfem_ctx* ctx, size_t* in_use, size_t* peak, int reset_peak);
 
 /* ---- sampled kernel timing (tracing; not part of the method) ------------------------------ *
  * Kernel classes: the sweep's dense contractions (local matvec, environments, projections) in
@@ -303,7 +326,8 @@ tnfem_status tnfem_op_env_left(tnfem_ctx* ctx, int ry0, int ry1, int rx0, int rx
  *    array's address cannot be obtained.
  *  - No cudaMalloc / cudaFree or other allocating routine is called.  The first call on each
  *    device looks up the array's device address (cudaGetSymbolAddress) with that device current;
- *    make that first call before any stream capture.
+ *    make that first call before any stream capture.  The address is kept for the life of the
+ *    process: do not reset the device (cudaDeviceReset) between calls.
  *  - All calls share the array: calls that overlap on the GPU race and must be serialised by the
  *    caller.  The array keeps the last call's contents; nothing in it needs to start at zero. */
 #define TNFEM_NOALLOC_SCRATCH_DOUBLES (1ll << 22)
@@ -327,6 +351,14 @@ tnfem_status tnfem_op_local_matvec_noalloc(void* stream, int r0, int n, int r1, 
 tnfem_status tnfem_op_local_cg(tnfem_ctx* ctx, int precision, int precond, int r0, int n, int r1, int a0,
                                int a1, const void* PhiL, const void* A, const void* PhiR, const void* g,
                                void* x, double rtol, int maxit, int* iters, int* state);
+/* Failure detection of the bounded device waits (no counterpart in the paper: the timeout path
+ * of the grid barriers that the solver's cooperative kernels use, made to run out on purpose).
+ * Launches `ctas` CTAs (1 <= ctas <= number of SMs) that pass three grid barriers whose waits are
+ * bounded by limit_ms (0.01 .. 2000); CTA `late_cta` (-1: none) first sleeps late_ms (0 .. 1000,
+ * bounded by the global timer) before its first arrival.  With late_ms beyond limit_ms the other
+ * CTAs give up, flag the error and leave, the late CTA leaves on arrival, and the call returns
+ * TNFEM_E_TIMEOUT; otherwise TNFEM_OK.  No wait is unbounded, and the context stays usable. */
+tnfem_status tnfem_op_barrier_probe(tnfem_ctx* ctx, int ctas, int late_cta, double late_ms, double limit_ms);
 /* Binary32 building blocks of the mixed-precision local solves (parity tests of both engines).
  * engine 0: CUDA-core FMA; engine 1: tcgen05 tensor cores, kind::tf32 with the three-term split
  * a b = a_hi b_hi + a_hi b_lo + a_lo b_hi (binary32-level accuracy from TF32 products), operands
@@ -372,6 +404,55 @@ tnfem_status tnfem_op_qr_ext(tnfem_ctx* ctx, int m, int rk, int w, double* A, do
  * largest magnitude is positive. */
 tnfem_status tnfem_op_svd(tnfem_ctx* ctx, int m, int n, const double* Ain, double* U, double* S,
                           double* Vt);
+
+/* ---- serving (continuous batching of solve requests on one GPU) ------------------------- *
+ * Not a step of the paper's method: a persistent request loop around tnfem_solve.  Requests of
+ * different dimension, levels, material, load and rank cap are queued as they arrive and admitted,
+ * in arrival order, when one of `workers` worker threads is idle and the sum of the memory
+ * estimates (tnfem_serve_estimate) of the admitted requests stays within `hbm_budget` (0: 80% of
+ * the device memory free at start); a request is always admitted when nothing else runs.  Each
+ * worker owns a context on its own non-blocking stream and allocates stream-ordered from the
+ * device's memory pool, so the admitted requests' kernels overlap on the device; each worker's
+ * cooperative kernels take 1/workers of the SMs.  A worker builds the request's operator and load
+ * (tnfem_build_stiffness / tnfem_build_load), solves (tnfem_solve) and copies the solution cores
+ * to host memory.  A request's result does not depend on what else runs: the same request solved
+ * alone or in the mix gives the same train up to rounding.
+ * Threading: submit, wait and result_take may be called from any host threads. */
+typedef struct tnfem_server tnfem_server;
+typedef struct {
+  tnfem_status status;        /* the request's own status (as tnfem_solve / the builders return) */
+  char message[256];          /* its error message when status != TNFEM_OK */
+  tnfem_solve_info info;
+  double queued_us, run_us, latency_us;  /* submit -> start, start -> end, submit -> end */
+  double start_us, end_us;    /* start and end relative to tnfem_server_start */
+  int worker;                 /* worker that ran it */
+  size_t est_bytes;           /* admission estimate */
+  size_t peak_bytes;          /* device memory the worker's context held at the request's peak */
+  int ncores;                 /* solution train: cores, ranks (ncores + 1), modes */
+  int ranks[64];
+  int modes[63];
+  size_t result_doubles;      /* doubles that tnfem_result_take copies out */
+} tnfem_request_info;
+/* Start `workers` (1..64) worker threads on `device`. */
+tnfem_status tnfem_server_start(int device, int workers, size_t hbm_budget, tnfem_server** out);
+/* The budget in force (hbm_budget, or the default chosen at start). */
+tnfem_status tnfem_server_budget(const tnfem_server* s, size_t* bytes);
+/* Upper estimate of the device memory one request holds at its peak (operator with its derived
+ * copies, environments, cores and local-solve workspace at the rank cap). */
+tnfem_status tnfem_serve_estimate(const tnfem_grid* grid, const tnfem_solve_opts* opts, size_t* bytes);
+/* Queue one request (arguments as for the builders and tnfem_solve; all host memory is copied,
+ * Fourier arrays included).  *id identifies it.  TNFEM_E_INVALID after tnfem_server_stop began. */
+tnfem_status tnfem_submit(tnfem_server* s, const tnfem_grid* grid, const tnfem_material* mat,
+                          const tnfem_load* loads, int n_loads, const tnfem_solve_opts* opts, uint64_t* id);
+/* Wait until request `id` is done (timeout_us < 0: no limit; TNFEM_E_TIMEOUT when it ran out) and
+ * fill *out (nullable).  The request's own outcome is out->status. */
+tnfem_status tnfem_wait(tnfem_server* s, uint64_t id, int64_t timeout_us, tnfem_request_info* out);
+/* Copy a finished request's solution cores (out->result_doubles doubles, cores in train order,
+ * layout of tnfem_tt_export; cores may be NULL to discard) and forget the request. */
+tnfem_status tnfem_result_take(tnfem_server* s, uint64_t id, double* cores);
+/* Stop: requests already admitted finish, queued ones end with TNFEM_E_INVALID; joins the workers
+ * and frees the server. */
+tnfem_status tnfem_server_stop(tnfem_server* s);
 
 #ifdef __cplusplus
 }

@@ -975,6 +975,9 @@ void Amen<T>::core_step(int k, AmenStats& st) {
   double rn2 = 0;
   TN_CHECK_CUDA(cudaMemcpyAsync(&rn2, c64_.p, sizeof(double), cudaMemcpyDeviceToHost, ctx_->stream));
   sync(ctx_);
+  if (!std::isfinite(gnorm) || !std::isfinite(rn2))
+    throw Error(TNFEM_E_NUMERIC, "non-finite local right-hand side or residual at core " + std::to_string(k) +
+                                     " (NaN/Inf in the operator, the load, the start or an environment)");
   const double res = gnorm > 0 ? std::sqrt(rn2) / gnorm : 0.0;
   max_res_ = std::max(max_res_, res);
   // r_ now holds g - B x_k; the binary32-local-solve path starts its refinement from it
@@ -996,6 +999,8 @@ void Amen<T>::core_step(int k, AmenStats& st) {
     TN_CHECK_CUDA(cudaMemcpyAsync(&dn2, c64_.p, sizeof(double), cudaMemcpyDeviceToHost, ctx_->stream));
     sync(ctx_);
     const double yn = nrm2<T>(ctx_, y_.p, N);
+    if (!std::isfinite(dn2) || !std::isfinite(yn))
+      throw Error(TNFEM_E_NUMERIC, "non-finite local solution at core " + std::to_string(k));
     if (yn > 0) max_dx_ = std::max(max_dx_, std::sqrt(dn2) / yn);
   }
   if (k == d - 1) {
@@ -1122,10 +1127,14 @@ void Amen<T>::run(AmenStats& st) {
   for (int sweep = 0; sweep < prm_.max_sweeps; ++sweep) {
     max_res_ = 0.0;
     max_dx_ = 0.0;
-    for (int k = 0; k < d; ++k) core_step(k, st);
+    for (int k = 0; k < d && !st.timed_out; ++k) {
+      core_step(k, st);
+      if (prm_.has_deadline && std::chrono::steady_clock::now() > prm_.deadline) st.timed_out = true;
+    }
     st.sweeps = sweep + 1;
     st.max_res = max_res_;
     st.max_dx = max_dx_;
+    if (st.timed_out) break;
     if (prm_.verbose)
       fprintf(stderr, "[tnfem] sweep %d: max res %.3e max dx %.3e rank %d iters %lld refines %lld fallbacks %lld\n",
               sweep, max_res_, max_dx_, *std::max_element(rx_.begin(), rx_.end()), iters_, local_refines_, fallbacks_);

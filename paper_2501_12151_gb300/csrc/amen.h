@@ -1,6 +1,7 @@
 // AMEn solve on the device (see amen.cu).
 #pragma once
 
+#include <chrono>
 #include <vector>
 
 #include "internal.h"
@@ -33,6 +34,9 @@ struct AmenParams {
   double stall_dx = 4.0;    // stop when updates are within stall_dx * tol and residuals stagnate
   uint64_t seed = 0;
   bool verbose = false;
+  // wall-clock limit of the solve (tnfem_solve_opts.timeout_us): checked after every core step
+  bool has_deadline = false;
+  std::chrono::steady_clock::time_point deadline;
 };
 
 // Phases of a core step timed when TNFEM_TRACE is set (see tnfem_solve_info.t_phase_ms).
@@ -55,6 +59,7 @@ struct AmenStats {
   double max_res = 0, max_dx = 0;
   double flops = 0;
   bool converged = false;
+  bool timed_out = false;  // the deadline passed; the iterate of the last completed core step is kept
   double phase_ms[kPhases] = {};
 };
 

@@ -173,7 +173,8 @@ int grid_dim_of(const tnfem_tt* u) {
 }
 
 tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_solve_opts* o,
-                      const tnfem_tt* x0, tnfem_solve_info* info, bool& converged) {
+                      const tnfem_tt* x0, tnfem_solve_info* info, bool& converged, bool has_deadline,
+                      std::chrono::steady_clock::time_point deadline, bool& timed_out) {
   // binary32 inner AMEn on A e = f - A u with binary64 source projections, binary64 rounding of u + e
   AmenParams ip;
   ip.tol = std::max(1e-5, std::min(1e-3, o->refine_tol * 1e2));
@@ -186,6 +187,8 @@ tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, con
   ip.local_rtol = o->local_rtol < 0 ? kLocalRtolDefault : o->local_rtol;
   ip.fused_cg = o->cg_engine == 0;
   ip.verbose = getenv("TNFEM_VERBOSE") != nullptr;
+  ip.has_deadline = has_deadline;
+  ip.deadline = deadline;
   tnfem_tt* u = x0 ? tt_clone(x0) : nullptr;
   const double fnorm = energy_norm(ctx, A, f, nullptr);  // scale reference (any norm works)
   (void)fnorm;
@@ -224,6 +227,10 @@ tnfem_tt* mixed_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, con
         converged = true;
         break;
       }
+    }
+    if (st.timed_out || (has_deadline && std::chrono::steady_clock::now() > deadline)) {
+      timed_out = true;
+      break;
     }
   }
   if (info) {
@@ -336,6 +343,20 @@ tnfem_status tnfem_set_stream(tnfem_ctx* ctx, void* stream) {
 
 long long tnfem_kernel_launches(const tnfem_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+tnfem_status tnfem_set_hbm_budget(tnfem_ctx* ctx, size_t bytes) {
+  if (!ctx) return TNFEM_E_INVALID;
+  ctx->mem_budget = bytes;
+  return TNFEM_OK;
+}
+
+tnfem_status tnfem_memory_stats(tnfem_ctx* ctx, size_t* in_use, size_t* peak, int reset_peak) {
+  if (!ctx) return TNFEM_E_INVALID;
+  if (reset_peak) ctx->mem_peak = ctx->mem_in_use;
+  if (in_use) *in_use = ctx->mem_in_use;
+  if (peak) *peak = ctx->mem_peak;
+  return TNFEM_OK;
+}
+
 tnfem_status tnfem_build_stiffness(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfem_material* mat,
                                    tnfem_mpo** out) {
   if (!ctx || !out) return TNFEM_E_INVALID;
@@ -403,7 +424,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
                          const tnfem_tt* x0, tnfem_tt** u, tnfem_solve_info* info) {
   if (!ctx || !u) return TNFEM_E_INVALID;
   *u = nullptr;
-  bool converged = false;
+  bool converged = false, timed_out = false;
   tnfem_status st = guard(ctx, [&] {
     TN_REQUIRE(A && f && opts, "null operator, load or options");
     TN_REQUIRE(A->d == f->d, "operator and load have different core counts");
@@ -415,14 +436,18 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
     TN_REQUIRE(opts->tol > 0 && opts->rank_cap >= 1 && opts->kickrank >= 0 && opts->max_sweeps >= 1,
                "solve options out of range");
     TN_REQUIRE(opts->precision == TNFEM_FP64 || opts->precision == TNFEM_MIXED ||
-                   opts->precision == TNFEM_MIXED_LOCAL,
+                   opts->precision == TNFEM_MIXED_LOCAL || opts->precision == TNFEM_MIXED_TF32,
                "precision");
+    TN_REQUIRE(opts->timeout_us >= 0, "timeout_us must be >= 0");
     sync(ctx);
-    EngineScope es(ctx, opts->tensor_cores ? 1 : 0);
+    EngineScope es(ctx, (opts->tensor_cores || opts->precision == TNFEM_MIXED_TF32) ? 1 : 0);
     auto t0 = std::chrono::steady_clock::now();
+    const bool has_deadline = opts->timeout_us > 0;
+    const auto deadline = t0 + std::chrono::microseconds(opts->timeout_us);
     tnfem_tt* res = nullptr;
     if (info) memset(info, 0, sizeof(*info));
-    if (opts->precision == TNFEM_FP64 || opts->precision == TNFEM_MIXED_LOCAL) {
+    if (opts->precision == TNFEM_FP64 || opts->precision == TNFEM_MIXED_LOCAL ||
+        opts->precision == TNFEM_MIXED_TF32) {
       AmenParams p;
       p.tol = opts->tol;
       p.rmax = opts->rank_cap;
@@ -433,11 +458,14 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
       p.precond = opts->no_precond == 0;
       p.local_rtol = opts->local_rtol < 0 ? kLocalRtolDefault : opts->local_rtol;
       p.fused_cg = opts->cg_engine == 0;
-      p.local_mixed = opts->precision == TNFEM_MIXED_LOCAL;
+      p.local_mixed = opts->precision != TNFEM_FP64;
       p.verbose = getenv("TNFEM_VERBOSE") != nullptr;
+      p.has_deadline = has_deadline;
+      p.deadline = deadline;
       AmenStats s;
       res = amen_solve(ctx, A, {AmenSource{f, false, 1.0}}, p, x0, false, s);
       converged = s.converged;
+      timed_out = s.timed_out;
       if (info) {
         info->sweeps = s.sweeps;
         info->local_iters = s.local_iters;
@@ -447,7 +475,7 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
         for (int i = 0; i < 7; ++i) info->t_phase_ms[i] = s.phase_ms[i];
       }
     } else {
-      res = mixed_solve(ctx, A, f, opts, x0, info, converged);
+      res = mixed_solve(ctx, A, f, opts, x0, info, converged, has_deadline, deadline, timed_out);
     }
     sync(ctx);
     auto t1 = std::chrono::steady_clock::now();
@@ -461,6 +489,10 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
     }
     *u = res;
   });
+  if (st == TNFEM_OK && timed_out) {
+    ctx->err = "solve stopped at its timeout_us";
+    return TNFEM_E_TIMEOUT;
+  }
   if (st == TNFEM_OK && !converged) {
     ctx->err = "solve stopped before reaching the tolerance";
     return TNFEM_E_NOT_CONVERGED;

@@ -32,6 +32,7 @@
 // A CG iteration thus costs three grid barriers (two-level, see grid_sync.cuh) and no launch.
 // Every barrier wait is bounded: on expiry the CTA records the error and leaves, and so does every
 // other CTA at its next barrier.
+#include <atomic>
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -776,11 +777,7 @@ __global__ void __launch_bounds__(FT, 2) fcg_kernel(const FcgArgs<U> A) {
   }
 }
 
-int sm_count(tnfem_ctx* ctx) {
-  int v = 0;
-  TN_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device));
-  return v;
-}
+int sm_count(tnfem_ctx* ctx) { return coop_sms(ctx); }
 
 }  // namespace
 
@@ -833,7 +830,7 @@ FcgPlan FusedCg::plan(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1, boo
   if (n < 1 || n > 8 || r0 < 1 || r1 < 1 || a0 < 1 || a1 < 1) return pl;
   if (rup4(r1) > FcgCfg<U>::PRB) return pl;  // one b' row of a PhiR slice must fit a staging buffer
   const int m = r0 * n;
-  static unsigned long long attr_set[2] = {0, 0};  // one bit per device and precision
+  static std::atomic<unsigned long long> attr_set[2];  // one bit per device and precision
   const unsigned long long bit = 1ull << (ctx->device & 63);
   const int which = sizeof(U) == 8 ? 1 : 0;
   constexpr int kSmemMax = 160 * 1024;

@@ -36,7 +36,8 @@ struct GridSync {
 
 // Waits until barrier `target` is complete or an error is flagged; thread 0 only.  Returns false
 // on error (its own timeout or another CTA's).
-__device__ __forceinline__ bool grid_wait_gen(GridSync* gs, unsigned int target) {
+__device__ __forceinline__ bool grid_wait_gen(GridSync* gs, unsigned int target,
+                                              unsigned long long limit_ns = kGridWaitNs) {
   volatile unsigned int* vgen = &gs->gen;
   const unsigned long long t0 = global_ns();
   unsigned int spins = 0;
@@ -44,7 +45,7 @@ __device__ __forceinline__ bool grid_wait_gen(GridSync* gs, unsigned int target)
     const unsigned int v = *vgen;
     if (v & kGridErrBit) return false;
     if (v >= target) return true;
-    if ((++spins & 63u) == 0 && global_ns() - t0 > kGridWaitNs) {
+    if ((++spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
       atomicOr(&gs->gen, kGridErrBit);
       return false;
     }
@@ -53,7 +54,7 @@ __device__ __forceinline__ bool grid_wait_gen(GridSync* gs, unsigned int target)
 
 // Flat barrier: every CTA arrives on gs->arrive.  idx: barriers this CTA has passed (all threads
 // keep it; it is incremented here).  True when all CTAs arrived and no error is flagged.
-__device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int& idx) {
+__device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int& idx, unsigned long long limit_ns = kGridWaitNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -64,7 +65,7 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int& idx) {
     if (old == target * gridDim.x - 1) {
       ok = (atomicAdd(&gs->gen, 1u) & kGridErrBit) == 0;
     } else {
-      ok = grid_wait_gen(gs, target);
+      ok = grid_wait_gen(gs, target, limit_ns);
     }
     fence_acq_rel_gpu();
     s_ok = ok ? 1 : 0;

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "tnfem.h"
@@ -77,6 +78,14 @@ struct tnfem_ctx {
   struct KTimerPool;
   KTimerPool* ktimers = nullptr;
   std::vector<ProfTimer> prof_timers;
+  // device-memory accounting: bytes held through dalloc, their high-water mark, and the budget
+  // (0: none) above which an allocation fails with TNFEM_E_BUDGET
+  size_t mem_budget = 0, mem_in_use = 0, mem_peak = 0;
+  std::unordered_map<void*, size_t> mem_sizes;
+  // SMs this context's cooperative (grid-barrier) kernels may fill (0: all).  Contexts whose work
+  // overlaps on one GPU (the serving loop's workers) each take a share, so that all their
+  // cooperative grids can be resident at once whatever order the hardware schedules them in.
+  int sm_share = 0;
 };
 
 namespace tnfem {
@@ -89,6 +98,8 @@ constexpr double kDfMinMnk = 1 << 20;
 inline int* df_overflow_flag(tnfem_ctx* ctx) { return reinterpret_cast<int*>(ctx->scratch + kScratchDoubles - 520); }
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs: partial sums of one reduction
 
+// SM count of the context's device, capped by ctx->sm_share (grid sizing of cooperative kernels)
+int coop_sms(tnfem_ctx* ctx);
 void* dalloc(tnfem_ctx* ctx, size_t bytes);
 void dfree(tnfem_ctx* ctx, void* p);
 void sync(tnfem_ctx* ctx);

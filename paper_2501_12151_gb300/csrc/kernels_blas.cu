@@ -5,6 +5,7 @@
 // contraction is ALU-bound: the GEMM below keeps all 152 SMs busy (split-K when the output is
 // small) and stages tiles through shared memory; memory traffic is secondary.
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.h"
 #include "tc_gemm.h"
@@ -456,8 +457,15 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
   int splits = 1;
   // split K only when the tiles alone fill well under one wave and K is long: the partial sums
   // cost a second kernel
-  const long long target = 152;
-  if (work && tiles < target / 2 && g.K >= 8 * BK) {
+  static const long long target = [] {
+    const char* e = getenv("TNFEM_SPLITK_TARGET");
+    return e ? std::max(1ll, atoll(e)) : 152ll;
+  }();
+  static const long long below = [] {
+    const char* e = getenv("TNFEM_SPLITK_BELOW");
+    return e ? std::max(1ll, atoll(e)) : 76ll;
+  }();
+  if (work && tiles < below && g.K >= 8 * BK) {
     long long want = (target + tiles - 1) / tiles;
     long long maxs = g.K / (2 * BK);
     long long fit = (long long)(work_elems / ((size_t)g.batch * g.M * g.N));

@@ -7,6 +7,7 @@
 // (qr_kernel, qr_blk_kernel, svd_kernel).  Cluster and CTA barriers are hardware barriers that
 // every thread reaches the same number of times; the grid barriers give up after a bounded wait
 // and report it.
+#include <atomic>
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -1052,7 +1053,7 @@ static bool qr_cluster(tnfem_ctx* ctx, int m, int n, const T* A, T* Q, T* R) {
   if (C < 2 || ncol > kQrClColMax) return false;
   const size_t smem = ((size_t)2 * ncol + 1) * m * sizeof(T);
   if (smem > kQrClSmemMax) return false;
-  static unsigned long long attr_set = 0;  // one bit per device
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   const unsigned long long bit = 1ull << (ctx->device & 63);
   if (!(attr_set & bit)) {
     if (cudaFuncSetAttribute(qr_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
@@ -1124,7 +1125,7 @@ void qr_ext(tnfem_ctx* ctx, int m, int rk, int w, T* A, T* Q, T* R, T* work, siz
   GridBar* bar = reinterpret_cast<GridBar*>(ctx->scratch + kScratchDoubles - 512);
   TN_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx->stream));
   int dev_sms = 0;
-  TN_CHECK_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  dev_sms = coop_sms(ctx);
   int ncta = std::max(1, std::min({64, dev_sms, (rk * w + (CT / 32) - 1) / (CT / 32)}));
   void* args[] = {&m, &rk, &w, &A, &Q, &R, &work, &bar};
   {
@@ -1181,7 +1182,7 @@ bool svd_cluster(tnfem_ctx* ctx, int m, int n, const T* A, T* U, T* S, T* Vt, in
   const size_t smem = ((size_t)ncol * (m + n) + n) * sizeof(T);
   constexpr size_t kMax = 160 * 1024;
   if (smem > kMax) return false;
-  static unsigned long long attr_set = 0;  // one bit per device
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   const unsigned long long bit = 1ull << (ctx->device & 63);
   if (!(attr_set & bit)) {
     if (cudaFuncSetAttribute(svd_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
@@ -1240,7 +1241,7 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
     }
     int ncta = (n + (n & 1)) / 2;
     int dev_sms = 0;
-    TN_CHECK_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    dev_sms = coop_sms(ctx);
     ncta = std::max(1, std::min(ncta, dev_sms));
     int max_sweeps = 60;
     void* args[] = {&m, &n, &A, &U, &S, &Vt, &G, &V, &sig, &max_sweeps, &bar};
@@ -1271,7 +1272,7 @@ void svd(tnfem_ctx* ctx, int m, int n, T* A, T* U, T* S, T* Vt, T* work) {
   ProfScope ps(ctx, TNFEM_PROF_SVD, 0.0, (double)(2 * m * n + 2 * n * n) * sizeof(T));
   const size_t smem = ((size_t)m * n + (size_t)n * n + n) * sizeof(T);
   const int use_smem = smem <= kSvdSmemMax ? 1 : 0;
-  static unsigned long long attr_set = 0;  // one bit per device
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   const unsigned long long bit = 1ull << (ctx->device & 63);
   if (use_smem && !(attr_set & bit)) {
     TN_CHECK_CUDA(cudaFuncSetAttribute(svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSvdSmemMax));

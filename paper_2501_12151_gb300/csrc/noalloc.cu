@@ -11,6 +11,9 @@
 // until the process exits.  Host code cannot use the symbol's name as a device address; the first
 // call on each device (made with that device current) looks the address up with
 // cudaGetSymbolAddress and caches it, so that first call should come before any stream capture.
+// The cached address belongs to the device's primary context: a cudaDeviceReset between calls
+// frees the array with that context, so the device must not be reset while this entry point is
+// in use (a reset is not detected).
 // Every call shares the array and overwrites it; calls whose work overlaps on the GPU (several
 // streams, several host threads) race on it and must be serialised by the caller.  Nothing in the
 // array has to start at zero: every element a call reads was written earlier by the same call.

@@ -15,6 +15,7 @@
 // elimination without pivoting (stable for SPD matrices).  Apply: one CTA per block multiplies
 // the block inverse with the block's strided slice of the residual, fused with the partial sums
 // of r.z that conjugate gradients needs.
+#include <atomic>
 #include <algorithm>
 
 #include "internal.h"
@@ -207,7 +208,7 @@ bool bj_setup(tnfem_ctx* ctx, int r0, int n, int r1, int a0, int a1, const T* Ph
     // the block stays on chip for the elimination when it fits
     const size_t smem_full = ((size_t)m * m + 2 * m) * sizeof(float);
     const int in_smem = smem_full <= kInvertSmemMax ? 1 : 0;
-    static unsigned long long attr_set = 0;  // one bit per device
+    static std::atomic<unsigned long long> attr_set{0};  // one bit per device
     const unsigned long long bit = 1ull << (ctx->device & 63);
     if (in_smem && !(attr_set & bit)) {
       TN_CHECK_CUDA(cudaFuncSetAttribute(bj_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -18,6 +18,7 @@
 //    owns lanes 32w..32w+31 = rows) and written to C with alpha / beta.
 // Every mbarrier wait is bounded: on expiry the kernel records an error, waits (bounded) for its
 // own MMAs, frees its TMEM and returns.
+#include <atomic>
 #include <algorithm>
 
 #include "internal.h"
@@ -243,7 +244,7 @@ template <int TN>
 void launch_tc(tnfem_ctx* ctx, const TcArgs& a, float alpha, const float* A, const float* B, float beta, float* C,
                float* work, int* err, const int* skip) {
   const int smem = 2 * stage_bytes<TN>() + 1024;
-  static unsigned long long attr_set = 0;  // one bit per device: the attribute is per device
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device: the attribute is per device
   const unsigned long long bit = 1ull << (ctx->device & 63);
   if (!(attr_set & bit)) {
     TN_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

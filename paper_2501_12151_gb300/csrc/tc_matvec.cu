@@ -21,6 +21,7 @@
 // split order by a small reduction kernel (deterministic, no atomics).  Every mbarrier wait is
 // bounded; on expiry the CTA records an error, skips its output, frees its tensor memory and
 // returns.
+#include <atomic>
 #include <algorithm>
 
 #include "internal.h"
@@ -235,7 +236,7 @@ constexpr int kSmem = STAGES * kStageBytes + 1024;
 
 template <int EPI>
 void launch_stage(tnfem_ctx* ctx, const StageArgs& a, int nrbA, int nrbB, int splits, double flops, double bytes) {
-  static unsigned long long attr_set = 0;
+  static std::atomic<unsigned long long> attr_set{0};
   const unsigned long long bit = 1ull << (ctx->device & 63);
   if (!(attr_set & bit)) {
     TN_CHECK_CUDA(cudaFuncSetAttribute(tc_stage_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));

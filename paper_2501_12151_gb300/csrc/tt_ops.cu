@@ -29,6 +29,9 @@ namespace tnfem {
 void* dalloc(tnfem_ctx* ctx, size_t bytes) {
   if (bytes == 0) bytes = 8;
   bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->mem_budget && ctx->mem_in_use + bytes > ctx->mem_budget)
+    throw Error(TNFEM_E_BUDGET, "device-memory budget of " + std::to_string(ctx->mem_budget) + " bytes exceeded (" +
+                                    std::to_string(ctx->mem_in_use) + " held, " + std::to_string(bytes) + " requested)");
   void* p = nullptr;
   if (ctx->alloc_fn) {
     p = ctx->alloc_fn(bytes, ctx->user);
@@ -40,13 +43,27 @@ void* dalloc(tnfem_ctx* ctx, size_t bytes) {
       throw Error(TNFEM_E_NOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
   }
+  ctx->mem_sizes[p] = bytes;
+  ctx->mem_in_use += bytes;
+  ctx->mem_peak = std::max(ctx->mem_peak, ctx->mem_in_use);
   return p;
 }
 
 void dfree(tnfem_ctx* ctx, void* p) {
   if (!p) return;
+  auto it = ctx->mem_sizes.find(p);
+  if (it != ctx->mem_sizes.end()) {
+    ctx->mem_in_use -= it->second;
+    ctx->mem_sizes.erase(it);
+  }
   if (ctx->free_fn) ctx->free_fn(p, ctx->user);
   else cudaFree(p);
+}
+
+int coop_sms(tnfem_ctx* ctx) {
+  int v = 0;
+  TN_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device));
+  return ctx->sm_share > 0 ? std::min(v, ctx->sm_share) : v;
 }
 
 void sync(tnfem_ctx* ctx) { TN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream)); }

@@ -49,7 +49,8 @@ class COpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("rank_cap", C.c_int), ("kickrank", C.c_int), ("max_sweeps", C.c_int),
                 ("precision", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int),
                 ("seed", C.c_uint64), ("local_maxit", C.c_int), ("no_precond", C.c_int),
-                ("tensor_cores", C.c_int), ("local_rtol", C.c_double), ("cg_engine", C.c_int)]
+                ("tensor_cores", C.c_int), ("local_rtol", C.c_double), ("cg_engine", C.c_int),
+                ("timeout_us", C.c_int64)]
 
 
 class CInfo(C.Structure):
@@ -65,6 +66,14 @@ class CInfo(C.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_phase_ms"}
         d["t_phase_ms"] = dict(zip(self.PHASES, list(self.t_phase_ms)))
         return d
+
+
+class CRequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("message", C.c_char * 256), ("info", CInfo),
+                ("queued_us", C.c_double), ("run_us", C.c_double), ("latency_us", C.c_double),
+                ("start_us", C.c_double), ("end_us", C.c_double), ("worker", C.c_int),
+                ("est_bytes", C.c_size_t), ("peak_bytes", C.c_size_t), ("ncores", C.c_int),
+                ("ranks", C.c_int * 64), ("modes", C.c_int * 63), ("result_doubles", C.c_size_t)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -90,6 +99,9 @@ _sig("tnfem_destroy", None, [_vp])
 _sig("tnfem_last_error", C.c_char_p, [_vp])
 _sig("tnfem_set_stream", _i, [_vp, _vp])
 _sig("tnfem_kernel_launches", C.c_longlong, [_vp])
+_sig("tnfem_set_hbm_budget", _i, [_vp, C.c_size_t])
+_sig("tnfem_memory_stats", _i, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), _i])
+_sig("tnfem_op_barrier_probe", _i, [_vp, _i, _i, _d, _d])
 _sig("tnfem_build_stiffness", _i, [_vp, C.POINTER(CGrid), C.POINTER(CMaterial), _pvp])
 _sig("tnfem_build_mass", _i, [_vp, C.POINTER(CGrid), _pvp])
 _sig("tnfem_build_load", _i, [_vp, C.POINTER(CGrid), C.POINTER(CMaterial), C.POINTER(CLoad), _i, _pvp])
@@ -128,6 +140,16 @@ _sig("tnfem_measure_fma_peak", _i, [_vp, _i, _pd])
 _sig("tnfem_profile_start", _i, [_vp, _i])
 _sig("tnfem_profile_read", _i, [_vp, _i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pd, _pd, _pd])
 
+_sig("tnfem_server_start", _i, [_i, _i, C.c_size_t, _pvp])
+_sig("tnfem_server_budget", _i, [_vp, C.POINTER(C.c_size_t)])
+_sig("tnfem_serve_estimate", _i, [C.POINTER(CGrid), C.POINTER(COpts), C.POINTER(C.c_size_t)])
+_sig("tnfem_submit", _i, [_vp, C.POINTER(CGrid), C.POINTER(CMaterial), C.POINTER(CLoad), _i, C.POINTER(COpts),
+                          C.POINTER(C.c_uint64)])
+_sig("tnfem_wait", _i, [_vp, C.c_uint64, C.c_int64, C.POINTER(CRequestInfo)])
+_sig("tnfem_result_take", _i, [_vp, C.c_uint64, _pd])
+_sig("tnfem_server_stop", _i, [_vp])
+
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed-local": 2, "mixed-tf32": 3}
 PROF_CLASSES = {"contract32": 0, "contract64": 1, "krylov": 2, "qr": 3, "svd": 4, "other": 5, "cg32": 6, "cg64": 7}
 
 
@@ -189,7 +211,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.rank_cap = int(o.rank_cap)
     co.kickrank = int(o.kickrank)
     co.max_sweeps = int(o.max_sweeps)
-    co.precision = {"fp64": 0, "mixed": 1, "mixed-local": 2}[o.precision]
+    co.precision = PRECISIONS[o.precision]
     co.refine_tol = float(o.refine_tol)
     co.max_refine = int(o.max_refine)
     co.seed = int(o.seed)
@@ -198,6 +220,7 @@ def c_opts(o: SolveOpts, local_maxit: int = 500) -> COpts:
     co.tensor_cores = 1 if getattr(o, "tensor_cores", False) else 0
     co.local_rtol = float(getattr(o, "local_rtol", -1.0))
     co.cg_engine = 0 if getattr(o, "fused_cg", True) else 1
+    co.timeout_us = int(getattr(o, "timeout_us", 0))
     return co
 
 
@@ -264,11 +287,24 @@ class Context:
     handle as int, 0 for the default stream).  With ``torch_alloc`` every device allocation
     of the library is served by PyTorch's caching allocator."""
 
-    def __init__(self, device: int = 0, stream: int = 0, torch_alloc: bool = False):
+    def __init__(self, device: int = 0, stream: int = 0, torch_alloc: bool = False, alloc_hook=None, free_hook=None):
         self._cbs = None
         alloc = ALLOC_FN()
         free = FREE_FN()
-        if torch_alloc:
+        if alloc_hook is not None:
+            # caller-supplied callbacks: alloc_hook(nbytes) -> device pointer (int) or 0 on failure,
+            # free_hook(ptr)
+            def _alloc(nbytes, user):
+                p = alloc_hook(int(nbytes))
+                return p or None
+
+            def _free(ptr, user):
+                free_hook(ptr)
+
+            alloc = ALLOC_FN(_alloc)
+            free = FREE_FN(_free)
+            self._cbs = (alloc, free)
+        elif torch_alloc:
             import torch
 
             def _alloc(nbytes, user):
@@ -304,6 +340,23 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib.tnfem_kernel_launches(self.h))
+
+    def set_hbm_budget(self, nbytes: int):
+        """Device-memory budget of the context in bytes (0: none)."""
+        self.check(lib.tnfem_set_hbm_budget(self.h, int(nbytes)))
+
+    def memory_stats(self, reset_peak: bool = False):
+        """(bytes held now, high-water mark)."""
+        a, b = C.c_size_t(), C.c_size_t()
+        self.check(lib.tnfem_memory_stats(self.h, C.byref(a), C.byref(b), 1 if reset_peak else 0))
+        return a.value, b.value
+
+    def barrier_probe(self, ctas: int, late_cta: int, late_ms: float, limit_ms: float) -> int:
+        """Status of tnfem_op_barrier_probe (0 or the TNFEM_E_TIMEOUT code); raises on other errors."""
+        st = lib.tnfem_op_barrier_probe(self.h, ctas, late_cta, late_ms, limit_ms)
+        if st not in (0, 5):
+            self.check(st)
+        return st
 
     def set_stream(self, stream: int):
         self.check(lib.tnfem_set_stream(self.h, C.c_void_p(stream)))
@@ -352,10 +405,15 @@ class Context:
         info = CInfo()
         co = c_opts(opts, local_maxit)
         st = lib.tnfem_solve(self.h, A.h, f.h, C.byref(co), x0.h if x0 else None, C.byref(out), C.byref(info))
-        if st == 4 and allow_not_converged and out.value:
-            return TT(self, out), info.as_dict()
+        if st in (4, 5) and allow_not_converged and out.value:
+            # not converged, or stopped at timeout_us: the last iterate and its info are returned
+            d = info.as_dict()
+            d["status"] = STATUS[st]
+            return TT(self, out), d
         self.check(st)
-        return TT(self, out), info.as_dict()
+        d = info.as_dict()
+        d["status"] = STATUS[st]
+        return TT(self, out), d
 
     def tt_import(self, cores: List[np.ndarray]) -> "TT":
         d = len(cores)
@@ -527,3 +585,71 @@ class Mpo:
         out = C.c_double()
         self.ctx.check(lib.tnfem_residual_norm(self.ctx.h, self.h, f.h, u.h, C.byref(out)))
         return out.value
+
+
+# ---------------------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------------------
+
+def serve_estimate(grid: Grid, opts: SolveOpts) -> int:
+    """Admission estimate (bytes) of one request."""
+    cg, co = c_grid(grid), c_opts(opts)
+    v = C.c_size_t()
+    _check(lib.tnfem_serve_estimate(C.byref(cg), C.byref(co), C.byref(v)))
+    return v.value
+
+
+class Server:
+    """Persistent request loop on one GPU (tnfem_server_*): ``submit`` queues a solve request and
+    returns its id, ``wait`` blocks until it is done and returns (cores or None, info dict)."""
+
+    def __init__(self, device: int = 0, workers: int = 2, hbm_budget: int = 0, local_maxit: int = 500):
+        h = C.c_void_p()
+        _check(lib.tnfem_server_start(device, workers, hbm_budget, C.byref(h)))
+        self.h = h
+        self.local_maxit = local_maxit
+
+    @property
+    def budget(self) -> int:
+        v = C.c_size_t()
+        _check(lib.tnfem_server_budget(self.h, C.byref(v)))
+        return v.value
+
+    def submit(self, grid: Grid, mat: Material, loads: Sequence[Load], opts: SolveOpts) -> int:
+        cg, cm = c_grid(grid), c_material(mat)
+        L = _Loads(loads, grid.dim)
+        co = c_opts(opts, self.local_maxit)
+        rid = C.c_uint64()
+        _check(lib.tnfem_submit(self.h, C.byref(cg), C.byref(cm), L.arr, L.n, C.byref(co), C.byref(rid)))
+        return rid.value
+
+    def wait(self, rid: int, timeout_us: int = -1, take: bool = True):
+        ri = CRequestInfo()
+        _check(lib.tnfem_wait(self.h, rid, timeout_us, C.byref(ri)))
+        d = {"status": STATUS[ri.status], "message": ri.message.decode(errors="replace"),
+             "info": ri.info.as_dict(), "queued_us": ri.queued_us, "run_us": ri.run_us,
+             "latency_us": ri.latency_us, "start_us": ri.start_us, "end_us": ri.end_us, "worker": ri.worker,
+             "est_bytes": ri.est_bytes, "peak_bytes": ri.peak_bytes}
+        cores = None
+        if take:
+            buf = np.zeros(max(1, ri.result_doubles))
+            _check(lib.tnfem_result_take(self.h, rid, buf.ctypes.data_as(_pd)))
+            if ri.result_doubles:
+                cores, off = [], 0
+                for k in range(ri.ncores):
+                    shp = (ri.ranks[k], ri.modes[k], ri.ranks[k + 1])
+                    sz = shp[0] * shp[1] * shp[2]
+                    cores.append(buf[off:off + sz].reshape(shp).copy())
+                    off += sz
+        return cores, d
+
+    def stop(self):
+        if getattr(self, "h", None):
+            lib.tnfem_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -83,7 +83,7 @@ class SolveOpts:
     rank_cap: int = 16
     kickrank: int = 4
     max_sweeps: int = 40
-    precision: str = "fp64"   # "fp64", "mixed" (outer TT-residual refinement) or "mixed-local"
+    precision: str = "fp64"   # "fp64", "mixed" (outer TT-residual refinement), "mixed-local" or "mixed-tf32"
     refine_tol: float = 1e-6
     max_refine: int = 20
     seed: int = 0
@@ -91,6 +91,7 @@ class SolveOpts:
     tensor_cores: bool = False  # binary32 contractions on the tcgen05 tensor cores
     local_rtol: float = -1.0    # local solves to this fraction of their starting residual (<0: default)
     fused_cg: bool = True       # local CG as one persistent kernel (False: a launch per step)
+    timeout_us: int = 0         # wall-clock limit of the solve (0: none)
 
 
 @dataclass
@@ -251,6 +252,6 @@ def served_requests(seed: int = 0, n: int = 512, rate: float = 200.0):
                       clamped=(True, False, False, False, False, False)),
             material=Material(E=(E, E), nu=nu),
             loads=[load],
-            opts=SolveOpts(tol=1e-6, rank_cap=cap, precision="mixed", seed=1000 + i),
+            opts=SolveOpts(tol=1e-6, rank_cap=cap, precision="mixed-local", seed=1000 + i),
         ))
     return arrivals, reqs

@@ -106,3 +106,26 @@ def test_fp64_bar_1e8_at_2_8(precision):
     ud = tt.to_natural_order(tt.tt_full(u.cores()), 2, 8)
     err = fem.energy_norm(Abc, ud - uh) / fem.energy_norm(Abc, uh)
     assert err <= 1e-8, (err, info)
+
+
+def test_3d_cantilever_2_4_both_bars():
+    """3D cantilever (gravity plus the seeded 8-mode Fourier force, trilinear elements) on 2^4 nodes
+    per axis, rank cap 64: the mixed path to 1e-6 and the binary64 path to 1e-8 against the
+    oracle's Galerkin solution.  (At 2^5 and beyond the cap of 64 binds: the solution needs larger
+    ranks at the middle bonds, and the error levels off at ~3e-3 for either precision.)"""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_12151_gb300 import tnfem
+    ctx = tnfem.Context(0)
+    pr = W.cantilever_3d(levels=4, rank_cap=64, tol=1e-6, precision="mixed-local")
+    Abc, fv = fem.system(pr.grid, pr.material, pr.loads)
+    uh = fem.solve(Abc, fv)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    for prec, tol, bar in (("mixed-local", 1e-6, 1e-6), ("fp64", 1e-8, 1e-8)):
+        o = W.cantilever_3d(levels=4, rank_cap=64, tol=tol, precision=prec).opts
+        o.max_sweeps = 30
+        u, info = ctx.solve(A, f, o)
+        ud = tt.to_natural_order(tt.tt_full(u.cores()), 3, 4)
+        err = fem.energy_norm(Abc, ud - uh) / fem.energy_norm(Abc, uh)
+        assert info["converged"] == 1 and err <= bar, (prec, err, info)

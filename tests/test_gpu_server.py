@@ -1,0 +1,106 @@
+"""The serving loop (continuous batching of solve requests on one GPU).
+
+A mixed set of small requests (2D and 3D, different levels, materials, loads and rank caps) is
+served by three workers.  Each result must equal, to rounding, the same request served alone by
+an otherwise idle server with the same worker count (so the same kernels and grid sizes), and
+must meet the solver's accuracy against the oracle's Galerkin solution.  Admission must keep the
+admitted estimates within the budget, each request's measured peak memory must stay within its
+estimate, and with room for several requests their runs must overlap in time.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, tt
+from paper_2501_12151_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _requests():
+    out = []
+    p = W.steel_plate_2d(levels=5, rank_cap=32, tol=1e-8, precision="mixed-local")
+    out.append(p)
+    p = W.manufactured_2d(levels=6, rank_cap=32, tol=1e-9)
+    p.opts.precision = "mixed-local"
+    out.append(p)
+    p = W.cantilever_3d(levels=3, rank_cap=64, tol=1e-8, precision="mixed-local")
+    out.append(p)
+    p = W.steel_plate_2d(levels=6, rank_cap=64, tol=1e-9, precision="fp64")
+    p.material = W.Material(E=(3e9, 3e9), nu=0.42)
+    out.append(p)
+    p = W.cantilever_paper_2d(levels=5, rank_cap=32, tol=1e-9, precision="mixed-local")
+    out.append(p)
+    p = W.steel_plate_2d(levels=7, rank_cap=32, tol=1e-8, precision="mixed-local")
+    p.loads = [W.Load(kind="traction", face=W.FACE_XHI, traction=(0.0, -2e6, 0.0))]
+    out.append(p)
+    return out
+
+
+@pytest.fixture(scope="module")
+def tn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_12151_gb300 import tnfem
+    return tnfem
+
+
+def _dense(cores, pr):
+    return tt.to_natural_order(tt.tt_full(cores), pr.grid.dim, pr.grid.levels)
+
+
+def test_results_same_alone_and_in_the_mix(tn):
+    reqs = _requests()
+    srv = tn.Server(0, workers=3)
+    alone = []
+    for pr in reqs:
+        rid = srv.submit(pr.grid, pr.material, pr.loads, pr.opts)
+        alone.append(srv.wait(rid))
+    ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for pr in reqs]
+    mix = [srv.wait(i) for i in ids]
+    srv.stop()
+    runs = sorted((m[1]["start_us"], m[1]["end_us"]) for m in mix)
+    assert any(runs[i + 1][0] < runs[i][1] for i in range(len(runs) - 1)), runs   # they overlapped
+    for pr, (ca, da), (cm, dm) in zip(reqs, alone, mix):
+        assert da["status"] == dm["status"] and dm["status"] in ("OK", "NOT_CONVERGED"), (pr.name, da, dm)
+        assert da["info"]["sweeps"] == dm["info"]["sweeps"], pr.name
+        ua, um = _dense(ca, pr), _dense(cm, pr)
+        assert np.linalg.norm(um - ua) <= 1e-12 * np.linalg.norm(ua), pr.name
+        Abc, fv = fem.system(pr.grid, pr.material, pr.loads)
+        uh = fem.solve(Abc, fv)
+        err = fem.energy_norm(Abc, um - uh) / fem.energy_norm(Abc, uh)
+        bar = 1e-4 if "paper" in pr.name else 1e-6
+        assert err <= bar, (pr.name, err, dm["info"])
+        assert dm["peak_bytes"] <= dm["est_bytes"], (pr.name, dm["peak_bytes"], dm["est_bytes"])
+
+
+def test_admission_keeps_estimates_within_budget(tn):
+    reqs = [pr for pr in _requests() if pr.grid.dim == 2]
+    est = [tn.serve_estimate(pr.grid, pr.opts) for pr in reqs]
+    budget = int(1.5 * max(est))            # never room for two of these at once
+    srv = tn.Server(0, workers=3, hbm_budget=budget)
+    assert srv.budget == budget
+    ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for pr in reqs]
+    res = [srv.wait(i, take=False)[1] for i in ids]
+    srv.stop()
+    for r in res:
+        assert r["status"] == "OK", r
+    # admitted in arrival order, one at a time
+    runs = sorted((r["start_us"], r["end_us"]) for r in res)
+    for a, b in zip(runs, runs[1:]):
+        assert b[0] >= a[1], runs
+    starts = [r["start_us"] for r in res]
+    assert starts == sorted(starts)
+
+
+def test_wait_timeout_and_stop_with_queued_requests(tn):
+    pr = W.steel_plate_2d(levels=8, rank_cap=32, tol=1e-9, precision="mixed-local")
+    srv = tn.Server(0, workers=1)
+    ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for _ in range(3)]
+    with pytest.raises(tn.TnfemError) as e:
+        srv.wait(ids[2], timeout_us=1000, take=False)    # still queued after 1 ms
+    assert e.value.status == 5
+    first = srv.wait(ids[0], take=False)[1]
+    assert first["status"] == "OK"
+    srv.stop()                                            # the rest finish or are refused
