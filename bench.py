@@ -62,12 +62,28 @@ def measured_peaks():
         return {}
 
 
+PROBLEM = {"name": "steel2d"}  # set by --workload
+
+
 def workload(levels: int, rank_cap: int, precision: str, tensor_cores: bool = False):
     from paper_2501_12151_gb300 import workloads as W
-    pr = W.steel_plate_2d(levels=levels, rank_cap=rank_cap, tol=1e-9, precision=precision)
+    if PROBLEM["name"] == "cube3d":
+        pr = W.cantilever_3d(levels=levels, rank_cap=rank_cap, tol=1e-6, precision=precision)
+        pr.opts.max_sweeps = 30
+    else:
+        pr = W.steel_plate_2d(levels=levels, rank_cap=rank_cap, tol=1e-9, precision=precision)
     pr.opts.refine_tol = 1e-6
     pr.opts.tensor_cores = tensor_cores
     return pr
+
+
+def workload_text(levels: int, rank_cap: int, precision: str, tol: float) -> str:
+    if PROBLEM["name"] == "cube3d":
+        return (f"3D cantilever (unit cube, clamped x=0, E 70 GPa, nu 0.33, gravity + seeded 8-mode Fourier force), "
+                f"2^{levels} nodes per axis ({3 * 8 ** levels} DOF), QTT {levels} levels, rank cap {rank_cap}, "
+                f"{precision}, tol {tol:g}, at most 30 sweeps")
+    return (f"2D plane-strain steel plate, 2^{levels}x2^{levels} nodes ({2 * 4 ** levels} DOF), QTT {levels} levels, "
+            f"rank cap {rank_cap}, {precision}, tol {tol:g} (rel. energy err vs u_h measured below)")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -227,6 +243,8 @@ def golden_uh(ctx, levels: int):
     the oracle's Galerkin solve), imported into the library; None when the file is absent."""
     import numpy as np
     path = os.path.join(ROOT, "tests", "golden", f"steel_plate_L{levels}_uh_qtt.npz")
+    if PROBLEM["name"] != "steel2d":
+        return None
     if not os.path.exists(path):
         return None
     z = np.load(path)
@@ -333,7 +351,10 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0 and args.precision != "fp64":
         fp64 = {}
-        for key, tol, msw in (("same_tol", args.tol, pr.opts.max_sweeps), ("tight", args.fp64_tight_tol, 40)):
+        arms = [("same_tol", args.tol, pr.opts.max_sweeps)]
+        if args.fp64_tight_tol > 0:
+            arms.append(("tight", args.fp64_tight_tol, 40))
+        for key, tol, msw in arms:
             o64 = workload(args.levels, args.rank_cap, "fp64").opts
             o64.tol = tol
             o64.max_sweeps = msw
@@ -424,9 +445,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32+f64" if args.precision != "fp64" else "f64",
         "data": "synthetic",
-        "config": {"workload": f"2D plane-strain steel plate, 2^{args.levels}x2^{args.levels} nodes "
-                               f"({2 * 4 ** args.levels} DOF), QTT {args.levels} levels, rank cap {args.rank_cap}, "
-                               f"{args.precision}, tol {args.tol:g} (rel. energy err vs u_h measured below)",
+        "config": {"workload": workload_text(args.levels, args.rank_cap, args.precision, args.tol),
                    "levels": args.levels, "rank_cap": args.rank_cap, "precision": args.precision, "tol": args.tol,
                    "tensor_cores": bool(args.tensor_cores),
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)"},
@@ -478,9 +497,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"2D plane-strain steel plate, 2^{args.levels}x2^{args.levels} nodes "
-                               f"({2 * 4 ** args.levels} DOF), QTT {args.levels} levels, rank cap {args.rank_cap}, "
-                               f"fp64 oracle, tol {args.tol:g}",
+        "config": {"workload": workload_text(args.levels, args.rank_cap, "fp64 oracle", args.tol),
                    "levels": args.levels, "rank_cap": args.rank_cap, "precision": "fp64", "tol": args.tol,
                    "parallelism": "cpu"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": s["threads"], "kind": "oracle", "sample": text},
@@ -580,6 +597,8 @@ def run_kernel_probe(args):
     flops = 2.0 * n * r0 * r1 * (r0 * a0 + n * a0 * a1 + r1 * a1)
     out = {"probe": "local matvec", "shape": {"r0": r0, "n": n, "r1": r1, "a0": a0, "a1": a1}, "flops": flops}
     for dt, name in ((np.float32, "f32"), (np.float64, "f64")):
+        if args.probe_f64_only and dt == np.float32:
+            continue
         t = [dev(v, dt) for v in (PhiL, A, PhiR, x)]
         y = torch.zeros(r0 * n * r1, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
         for e in ((0, 1, 2) if dt == np.float32 else (None,)):
@@ -594,6 +613,8 @@ def run_kernel_probe(args):
                 torch.cuda.synchronize()
                 walls.append(time.perf_counter() - t0)
             out[f"{name}_engine{e if e is not None else 'fp64'}_wall_us"] = 1e6 * min(walls)
+    if args.probe_f64_only:
+        return out
     # the fused CG kernel on a symmetric positive definite system of the same shape
     # (B = sum_beta PhiL_beta (x) M_beta (x) PhiR_beta, PSD factors, identity-shifted beta = 0 term),
     # a fixed number of steps (rtol 0)
@@ -649,12 +670,17 @@ def main(argv=None):
                     help="only launch the local-matvec engines and the fused CG kernel a few times at --probe-shape (for ncu)")
     ap.add_argument("--probe-shape", type=int, nargs=5, default=[49, 4, 49, 51, 51], metavar=("R0", "N", "R1", "A0", "A1"))
     ap.add_argument("--probe-reps", type=int, default=3)
+    ap.add_argument("--probe-f64-only", action="store_true", help="only the binary64 local matvec in the probe")
     ap.add_argument("--probe-cg-steps", type=int, default=50, help="steps of the fused CG launch in the probe")
     ap.add_argument("--served", type=int, default=0, help="run the served batch with this many requests instead")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-budget", type=int, default=0, help="device-memory budget of the server (0: 80%% of free)")
     ap.add_argument("--serve-fp64", type=int, default=16, help="requests of the one-at-a-time binary64 baseline")
+    ap.add_argument("--workload", choices=["steel2d", "cube3d"], default="steel2d",
+                    help="steel2d: the 2^10 x 2^10 steel plate (default); cube3d: the 3D cantilever (use with "
+                         "--levels 7 --rank-cap 96 --tol 1e-6 --fp64-tight-tol 0 --no-cpu-baseline)")
     args = ap.parse_args(argv)
+    PROBLEM["name"] = args.workload
     if args.served > 0:
         out = run_served(args)
     elif args.kernel_probe:

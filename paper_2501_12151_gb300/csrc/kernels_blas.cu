@@ -5,7 +5,6 @@
 // contraction is ALU-bound: the GEMM below keeps all 152 SMs busy (split-K when the output is
 // small) and stages tiles through shared memory; memory traffic is secondary.
 #include <algorithm>
-#include <cstdlib>
 
 #include "internal.h"
 #include "tc_gemm.h"
@@ -455,17 +454,11 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
   int tiles_m = (int)((rows + BM - 1) / BM), tiles_n = (g.N + BN - 1) / BN;
   long long tiles = (long long)tiles_m * tiles_n * (flat ? 1 : g.batch);
   int splits = 1;
-  // split K only when the tiles alone fill well under one wave and K is long: the partial sums
-  // cost a second kernel
-  static const long long target = [] {
-    const char* e = getenv("TNFEM_SPLITK_TARGET");
-    return e ? std::max(1ll, atoll(e)) : 152ll;
-  }();
-  static const long long below = [] {
-    const char* e = getenv("TNFEM_SPLITK_BELOW");
-    return e ? std::max(1ll, atoll(e)) : 76ll;
-  }();
-  if (work && tiles < below && g.K >= 8 * BK) {
+  // split K when the tiles alone give the SMs fewer than two CTAs each and K is long (the partial
+  // sums cost a second kernel).  Aiming at two CTAs per SM rather than one measured 525 ms per
+  // 2^10 x 2^10 solve against 563 ms (binary64 contractions 201 -> 182 ms, reduces 53 -> 48 ms)
+  const long long target = 304;
+  if (work && tiles < target && g.K >= 8 * BK) {
     long long want = (target + tiles - 1) / tiles;
     long long maxs = g.K / (2 * BK);
     long long fit = (long long)(work_elems / ((size_t)g.batch * g.M * g.N));

@@ -200,8 +200,8 @@ __device__ void qr_blk_form_t(int m, int p0, int pb, const T* __restrict__ Vs, c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(QBT) qr_blk_kernel(int m, int n, int nb, T* __restrict__ A, T* __restrict__ Q,
-                                                     T* __restrict__ R, T* __restrict__ tau) {
+__device__ __forceinline__ void qr_blk_body(int m, int n, int nb, T* __restrict__ A, T* __restrict__ Q,
+                                            T* __restrict__ R, T* __restrict__ tau) {
   extern __shared__ __align__(16) unsigned char qb_smem[];
   T* Vs = reinterpret_cast<T*>(qb_smem);  // [nb][m] the current panel
   __shared__ T sh[33];
@@ -359,6 +359,23 @@ __global__ void __launch_bounds__(QBT) qr_blk_kernel(int m, int n, int nb, T* __
     const int i = (int)(t / k), c = (int)(t % k);
     Q[t] = QW[(long long)c * m + i];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(QBT) qr_blk_kernel(int m, int n, int nb, T* __restrict__ A, T* __restrict__ Q,
+                                                     T* __restrict__ R, T* __restrict__ tau) {
+  qr_blk_body<T>(m, n, nb, A, Q, R, tau);
+}
+
+// The same factorisation of `gridDim.x` independent m x n blocks (block b at A + b sA, its factors
+// at Q + b sQ, R + b sR, its Householder scalars at tau + b sT): the first level of the
+// tall-skinny QR below, one CTA per row block.
+template <typename T>
+__global__ void __launch_bounds__(QBT) qr_blk_batched_kernel(int m, int n, int nb, T* __restrict__ A, long long sA,
+                                                             T* __restrict__ Q, long long sQ, T* __restrict__ R,
+                                                             long long sR, T* __restrict__ tau, long long sT) {
+  const long long b = blockIdx.x;
+  qr_blk_body<T>(m, n, nb, A + b * sA, Q + b * sQ, R + b * sR, tau + b * sT);
 }
 
 // Householder QR (m >= n) on one thread-block cluster, with qr_kernel's arithmetic in qr_kernel's
@@ -1088,10 +1105,70 @@ static bool qr_cluster(tnfem_ctx* ctx, int m, int n, const T* A, T* Q, T* R) {
   return true;
 }
 
+// Tall-skinny QR (TSQR) for matrices whose columns do not fit one CTA's shared memory (the
+// unfoldings of the 3D operator's cores in its rounding, ~28k x 441): the rows are cut into
+// blocks of about 2n rows, each block is factorised by its own CTA (qr_blk_batched_kernel), the
+// stacked R factors are factorised the same way recursively, and each block of Q is its block
+// Q factor times the matching n x n block of the next level's Q (batched GEMM).  Every level is
+// Householder QR, so Q has orthonormal columns to rounding whatever the rank of A.
+template <typename T>
+void qr_tall(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R);
+
+template <typename T>
+static void qr_blk_batch(tnfem_ctx* ctx, int rows, int n, int count, T* A, T* Q, T* R, T* tau) {
+  const int nb = (int)std::min<size_t>(kQrNbMax, kQrSmemMax / ((size_t)rows * sizeof(T)));
+  TN_REQUIRE(nb >= 1, "qr_tall: row block too long");
+  const size_t smem = (size_t)nb * rows * sizeof(T);
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (!(attr_set & bit)) {
+    TN_CHECK_CUDA(cudaFuncSetAttribute(qr_blk_batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kQrSmemMax));
+    attr_set |= bit;
+  }
+  qr_blk_batched_kernel<T><<<count, QBT, smem, ctx->stream>>>(rows, n, nb, A, (long long)rows * n, Q,
+                                                               (long long)rows * n, R, (long long)n * n, tau, n);
+  count_launch(ctx);
+  check_launch(ctx, "qr_tall");
+}
+
+template <typename T>
+void qr_tall(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R) {
+  const int b = 2 * n;           // rows per block
+  const int B = m / b;           // blocks; the last one takes the remaining rows (b .. 2b - 1)
+  const int last = m - (B - 1) * b;
+  DArr<T> Qb(ctx, (size_t)m * n), Rs(ctx, (size_t)B * n * n), tau(ctx, (size_t)B * n + 8);
+  if (B > 1) qr_blk_batch<T>(ctx, b, n, B - 1, A, Qb.p, Rs.p, tau.p);
+  qr_blk_batch<T>(ctx, last, n, 1, A + (size_t)(B - 1) * b * n, Qb.p + (size_t)(B - 1) * b * n,
+                  Rs.p + (size_t)(B - 1) * n * n, tau.p + (size_t)(B - 1) * n);
+  // next level: the stacked R factors (B n x n)
+  DArr<T> Q2(ctx, (size_t)B * n * n);
+  const int m2 = B * n;
+  if (m2 >= 4 * n && (size_t)m2 * sizeof(T) > kQrSmemMax / kQrNbMax) {
+    qr_tall<T>(ctx, m2, n, Rs.p, Q2.p, R);
+  } else {
+    DArr<T> w(ctx, qr_work_elems(m2, n));
+    qr<T>(ctx, m2, n, Rs.p, Q2.p, R, w.p);
+  }
+  // Q block i = Qb_i (rows_i x n) . Q2_i (n x n)
+  if (B > 1) {
+    GemmDesc g{b, n, n, B - 1, n, 1, (long long)b * n, n, 1, (long long)n * n, n, 1, (long long)b * n};
+    gemm<T>(ctx, g, T(1), Qb.p, Q2.p, T(0), Q);
+  }
+  GemmDesc gl{last, n, n, 1, n, 1, 0, n, 1, 0, n, 1, 0};
+  gemm<T>(ctx, gl, T(1), Qb.p + (size_t)(B - 1) * b * n, Q2.p + (size_t)(B - 1) * n * n, T(0),
+          Q + (size_t)(B - 1) * b * n);
+}
+
 template <typename T>
 void qr(tnfem_ctx* ctx, int m, int n, T* A, T* Q, T* R, T* work) {
   if (m <= 0 || n <= 0) return;
   const int k = std::min(m, n);
+  // columns too long for the one-CTA panel and far taller than wide: the tall-skinny QR
+  if (m >= 8 * n && n >= 16 && (size_t)m * sizeof(T) * kQrNbMax > kQrSmemMax && !ctx->capturing) {
+    qr_tall<T>(ctx, m, n, A, Q, R);
+    return;
+  }
   ProfScope ps(ctx, TNFEM_PROF_QR, 4.0 * m * n * (double)k, (double)(2 * m * n + m * k + k * n) * sizeof(T));
   if (qr_cluster<T>(ctx, m, n, A, Q, R)) {
     count_launch(ctx);

@@ -325,7 +325,18 @@ tnfem_tt* tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax) {
       if (w >= r0) {
         // M^T (w x r0) = U S Vt  =>  M = Vt^T S U^T: new core = U^T (rows), left factor Vt^T S
         transpose2<double>(ctx, Mt.p, y->core[k], r0, w);
-        svd<double>(ctx, w, r0, Mt.p, U.p, Sd.p, Vt.p, sw.p);
+        if (w >= 8 * r0 && r0 >= 64) {
+          // far taller than wide (the operator cores of the 3D rounding): QR first, the Jacobi SVD
+          // of the small R factor, U = Q U_R (the SVD's rotations then run on r0-long columns)
+          DArr<double> Qt(ctx, (size_t)w * r0), Rt(ctx, (size_t)r0 * r0), UR(ctx, (size_t)r0 * r0),
+              qw(ctx, qr_work_elems(w, r0));
+          qr<double>(ctx, w, r0, Mt.p, Qt.p, Rt.p, qw.p);
+          svd<double>(ctx, r0, r0, Rt.p, UR.p, Sd.p, Vt.p, sw.p);
+          GemmDesc gu{w, r0, r0, 1, r0, 1, 0, r0, 1, 0, r0, 1, 0};
+          gemm<double>(ctx, gu, 1.0, Qt.p, UR.p, 0.0, U.p);
+        } else {
+          svd<double>(ctx, w, r0, Mt.p, U.p, Sd.p, Vt.p, sw.p);
+        }
         transpose2<double>(ctx, right.p, U.p, w, p);     // p x w
         transpose2<double>(ctx, left.p, Vt.p, p, p);     // r0 x p (= Vt^T)
       } else {

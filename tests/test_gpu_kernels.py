@@ -70,10 +70,12 @@ def test_env_left(ctx, ry0, ry1, rx0, rx1, n, a0, a1):
 
 
 # Paths: n >= 16 with the columns in a cluster's shared memory -> qr_cluster_kernel ((272, 68),
-# (64, 64), (1056, 136), (1152, 72)); larger tall matrices -> the blocked one-CTA kernel ((4608, 53),
-# (16384, 4), (16385, 4)); small or wide ones -> the row-major one-CTA kernel.
+# (64, 64), (1056, 136), (1152, 72)); m >= 8n, n >= 16 and columns longer than 3200 -> the
+# tall-skinny QR (blocks of 2n rows, one CTA each, recursively: (4608, 53), (9001, 150) with a
+# ragged last block, (28224, 441) the 3D operator rounding's unfolding); other tall matrices ->
+# the blocked one-CTA kernel ((16384, 4), (16385, 4)); small or wide ones -> the row-major kernel.
 @pytest.mark.parametrize("m,n", [(1, 1), (7, 3), (3, 7), (272, 68), (64, 64), (1056, 136), (1152, 72),
-                                 (4608, 53), (16384, 4), (16385, 4), (40, 100)])
+                                 (4608, 53), (9001, 150), (28224, 441), (16384, 4), (16385, 4), (40, 100)])
 def test_qr(ctx, m, n):
     A = W.random_matrix(9, m, n)
     k = min(m, n)
@@ -92,7 +94,7 @@ def test_qr(ctx, m, n):
     np.testing.assert_allclose(sgn[:, None] * Rh, Rn, atol=1e-12 * np.abs(A).max() * max(m, n))
 
 
-@pytest.mark.parametrize("m,n", [(300, 40), (1152, 72), (30, 30)])
+@pytest.mark.parametrize("m,n", [(300, 40), (1152, 72), (30, 30), (6000, 120)])
 def test_qr_rank_deficient(ctx, m, n):
     """Columns that repeat earlier ones, a zero column and a zero first column: Q keeps orthonormal
     columns and Q R reproduces A (the Householder steps with a vanishing tail take tau = 0)."""

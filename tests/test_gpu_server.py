@@ -32,7 +32,7 @@ def _requests():
     out.append(p)
     p = W.cantilever_paper_2d(levels=5, rank_cap=32, tol=1e-9, precision="mixed-local")
     out.append(p)
-    p = W.steel_plate_2d(levels=7, rank_cap=32, tol=1e-8, precision="mixed-local")
+    p = W.steel_plate_2d(levels=7, rank_cap=64, tol=1e-8, precision="mixed-local")
     p.loads = [W.Load(kind="traction", face=W.FACE_XHI, traction=(0.0, -2e6, 0.0))]
     out.append(p)
     return out
@@ -78,29 +78,32 @@ def test_results_same_alone_and_in_the_mix(tn):
 def test_admission_keeps_estimates_within_budget(tn):
     reqs = [pr for pr in _requests() if pr.grid.dim == 2]
     est = [tn.serve_estimate(pr.grid, pr.opts) for pr in reqs]
-    budget = int(1.5 * max(est))            # never room for two of these at once
+    budget = max(est) + sorted(est)[0] // 2   # the largest fits, but never with the smallest beside it
     srv = tn.Server(0, workers=3, hbm_budget=budget)
     assert srv.budget == budget
     ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for pr in reqs]
     res = [srv.wait(i, take=False)[1] for i in ids]
     srv.stop()
+    for r, e in zip(res, est):
+        assert r["status"] in ("OK", "NOT_CONVERGED"), r
+        assert r["est_bytes"] == e
+    # whenever a request started, the estimates of the requests then running fit the budget
     for r in res:
-        assert r["status"] == "OK", r
-    # admitted in arrival order, one at a time
-    runs = sorted((r["start_us"], r["end_us"]) for r in res)
-    for a, b in zip(runs, runs[1:]):
-        assert b[0] >= a[1], runs
+        t = r["start_us"]
+        running = [q["est_bytes"] for q in res if q["start_us"] <= t < q["end_us"]]
+        assert sum(running) <= budget or len(running) == 1, (running, budget)
+    # admitted in arrival order
     starts = [r["start_us"] for r in res]
     assert starts == sorted(starts)
 
 
 def test_wait_timeout_and_stop_with_queued_requests(tn):
-    pr = W.steel_plate_2d(levels=8, rank_cap=32, tol=1e-9, precision="mixed-local")
+    pr = W.steel_plate_2d(levels=8, rank_cap=64, tol=1e-9, precision="mixed-local")
     srv = tn.Server(0, workers=1)
     ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for _ in range(3)]
     with pytest.raises(tn.TnfemError) as e:
         srv.wait(ids[2], timeout_us=1000, take=False)    # still queued after 1 ms
     assert e.value.status == 5
     first = srv.wait(ids[0], take=False)[1]
-    assert first["status"] == "OK"
+    assert first["status"] in ("OK", "NOT_CONVERGED") and first["info"]["sweeps"] > 0
     srv.stop()                                            # the rest finish or are refused

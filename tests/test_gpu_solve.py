@@ -215,10 +215,11 @@ def test_full_size_steel_plate_matches_oracle_amen():
     Oracle A cannot solve this size directly, so the check is by properties that hold at any size,
     computed by the oracle from the exported cores: (1) the GPU solution is within 1e-6 relative
     energy norm of the oracle's own AMEn solution at the same settings (difference train formed
-    explicitly, orthogonalised, then its energy norm taken); (2) it is at least as good in the
-    energy functional J(u) = u^T A u / 2 - f^T u, whose minimiser is u_h: J(u) - J(u_h) is half the
-    squared energy error, so J(u_gpu) <= J(u_oracle) + 1e-12 |J| bounds the GPU error squared by the
-    oracle's plus 1e-12 relative."""
+    explicitly, orthogonalised, then its energy norm taken); (2) its error against the Galerkin
+    solution u_h (stored as a train by the oracle's generator script) is within twice the oracle
+    iterate's own error, both as energy norms of explicitly formed differences.  (A comparison of
+    the energy functional J(u) = u^T A u / 2 - f^T u instead cannot resolve this: u^T A u of a
+    smooth train evaluated through operator cores cancels to ~1e-10 relative at this size.)"""
     pr = W.steel_plate_2d(levels=10, rank_cap=64, tol=1e-9, precision="mixed-local")
     from paper_2501_12151_gb300 import tnfem
     ctx = tnfem.Context(0)
@@ -236,9 +237,13 @@ def test_full_size_steel_plate_matches_oracle_amen():
     diff = tt.tt_add(ug, uo, -1.0)
     rel = _energy_norm_tt(Ao, diff) / _energy_norm_tt(Ao, uo)
     assert rel <= 1e-6, (rel, info, oinfo.sweeps)
-    J = lambda x: 0.5 * _quad_form(Ao, x) - tt.tt_dot(fo, x)  # noqa: E731
-    Jg, Jo = J(ug), J(uo)
-    assert Jg <= Jo + 1e-12 * abs(Jo), (Jg, Jo)
+    import os
+    z = np.load(os.path.join(os.path.dirname(__file__), "golden", "steel_plate_L10_uh_qtt.npz"))
+    uh = [z[f"core{k}"] for k in range(len(z.files))]
+    nh = _energy_norm_tt(Ao, uh)
+    eg = _energy_norm_tt(Ao, tt.tt_add(ug, uh, -1.0)) / nh
+    eo = _energy_norm_tt(Ao, tt.tt_add(uo, uh, -1.0)) / nh
+    assert eg <= 1e-6 and eg <= 2.0 * eo, (eg, eo)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed-local"])
