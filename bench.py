@@ -392,9 +392,16 @@ def run_ours(args):
     cls = max(device_ms, key=lambda c: device_ms[c])
     p = prof[cls]
     bf16 = pk.get("bf16_tflops")
+    df_route = args.precision in ("mixed-local", "mixed-tf32") and args.tol >= 1e-7
     if cls in ("contract32", "cg32"):
         peak = fp32_simt_peak_gflops() * 1e-3
         peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (CUDA-core binary32 FMA)"
+    elif cls == "contract64" and df_route:
+        # at loose tolerances the mixed path runs its large binary64 contractions in double-binary32
+        # arithmetic: 12 binary32 instructions per emulated multiply-add
+        peak = fp32_simt_peak_gflops() * 1e-3 / 12.0
+        peak_note = ("derived: binary32 FMA peak (152 SMs x 128 lanes x 2 flop x 2070 MHz) / 12 binary32 "
+                     "instructions per double-binary32 multiply-add (the class also holds small binary64 launches)")
     elif bf16:
         peak = bf16 * FP64_NOMINAL_GFLOPS / 2.25e6
         peak_note = (f"of measured: MEASURED_PEAKS bf16 {bf16} TFLOP/s x nominal binary64/bf16 ratio 1.25/2250 "
@@ -568,7 +575,12 @@ def run_served(args):
                    "mean_run_ms": float(np.mean([r["run_us"] for r in res])) * 1e-3,
                    "mean_queued_ms": float(np.mean([r["queued_us"] for r in res])) * 1e-3,
                    "peak_within_estimate": all(r["peak_bytes"] <= r["est_bytes"] for r in res),
-                   "statuses": sorted({r["status"] for r in res})},
+                   "statuses": sorted({r["status"] for r in res}),
+                   "requests": [{"dim": pr.grid.dim, "levels": pr.grid.levels, "cap": pr.opts.rank_cap,
+                                 "status": r["status"], "run_ms": round(r["run_us"] * 1e-3, 1),
+                                 "latency_ms": round(r["latency_us"] * 1e-3, 1), "sweeps": r["info"]["sweeps"],
+                                 "est_MiB": r["est_bytes"] >> 20, "peak_MiB": r["peak_bytes"] >> 20}
+                                for pr, r in zip(reqs, res)]},
         "one_at_a_time_fp64": {"requests": len(seq), "solves_per_s": len(seq) / t_seq if seq else None,
                                "p50_ms": sorted(seq)[len(seq) // 2] if seq else None},
         "clocks": clk.summary(),

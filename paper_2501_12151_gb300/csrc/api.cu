@@ -441,6 +441,15 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
     TN_REQUIRE(opts->timeout_us >= 0, "timeout_us must be >= 0");
     sync(ctx);
     EngineScope es(ctx, (opts->tensor_cores || opts->precision == TNFEM_MIXED_TF32) ? 1 : 0);
+    // Mixed paths at a loose tolerance run their large binary64 contractions in double-binary32
+    // arithmetic (binary32 FMAs issue at 64x the binary64 rate on this part): its ~2^-47 noise,
+    // amplified by the local systems' conditioning, stays orders of magnitude below a tolerance of
+    // 1e-7 or looser, whereas at 1e-9 it stalled the stopping rule (measured).  A contraction whose
+    // values leave the binary32 range sets a flag, and the solve is then repeated in binary64.
+    const bool df_route = (opts->precision == TNFEM_MIXED_LOCAL || opts->precision == TNFEM_MIXED_TF32) &&
+                          opts->tol >= kDfTolMin;
+    DfScope dfs(ctx, df_route);
+    if (df_route) TN_CHECK_CUDA(cudaMemsetAsync(df_overflow_flag(ctx), 0, sizeof(int), ctx->stream));
     auto t0 = std::chrono::steady_clock::now();
     const bool has_deadline = opts->timeout_us > 0;
     const auto deadline = t0 + std::chrono::microseconds(opts->timeout_us);
@@ -464,6 +473,18 @@ tnfem_status tnfem_solve(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, 
       p.deadline = deadline;
       AmenStats s;
       res = amen_solve(ctx, A, {AmenSource{f, false, 1.0}}, p, x0, false, s);
+      if (df_route) {
+        int ovf = 0;
+        TN_CHECK_CUDA(cudaMemcpyAsync(&ovf, df_overflow_flag(ctx), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        sync(ctx);
+        if (ovf) {  // a value outside the binary32 range: the whole solve again in binary64
+          delete res;
+          res = nullptr;
+          ctx->df64 = false;
+          s = AmenStats();
+          res = amen_solve(ctx, A, {AmenSource{f, false, 1.0}}, p, x0, false, s);
+        }
+      }
       converged = s.converged;
       timed_out = s.timed_out;
       if (info) {

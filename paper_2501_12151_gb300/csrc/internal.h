@@ -94,6 +94,8 @@ constexpr int kScratchDoubles = 1 << 16;
 // binary64 GEMMs with at least this many multiply-adds run in double-binary32 when ctx->df64
 // (tnfem_op_gemm_f64 engine 1; the solve does not use it, see the engine's description)
 constexpr double kDfMinMnk = 1 << 20;
+// the mixed solve paths take the double-binary32 route for tolerances from this value up
+constexpr double kDfTolMin = 1e-7;
 // device flag (in the context's scratch) set by a double-binary32 GEMM whose output was not finite
 inline int* df_overflow_flag(tnfem_ctx* ctx) { return reinterpret_cast<int*>(ctx->scratch + kScratchDoubles - 520); }
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs: partial sums of one reduction

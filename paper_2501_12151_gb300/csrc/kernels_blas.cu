@@ -458,15 +458,36 @@ void gemm(tnfem_ctx* ctx, const GemmDesc& g, T alpha, const T* A, const T* B, T 
   // sums cost a second kernel).  Aiming at two CTAs per SM rather than one measured 525 ms per
   // 2^10 x 2^10 solve against 563 ms (binary64 contractions 201 -> 182 ms, reduces 53 -> 48 ms)
   const long long target = 304;
-  if (work && tiles < target && g.K >= 8 * BK) {
-    long long want = (target + tiles - 1) / tiles;
-    long long maxs = g.K / (2 * BK);
-    long long fit = (long long)(work_elems / ((size_t)g.batch * g.M * g.N));
-    splits = (int)std::max<long long>(1, std::min(std::min(want, maxs), std::min(fit, (long long)64)));
+  int kchunk = g.K;
+  if constexpr (sizeof(T) == 8) {
+    // binary64: one CTA already keeps an SM's FP64 pipe busy (ncu: 92-98% active with one CTA
+    // resident), so an SM's time is the sum of its CTAs' K steps.  Take the split that minimises
+    // the busiest SM's steps, ceil(CTAs / SMs) x ceil(ceil(K / s) / BK), the fewest splits on ties
+    // (each split adds partial sums to reduce).
+    const long long fit = work ? (long long)(work_elems / ((size_t)g.batch * g.M * g.N)) : 1;
+    const long long smax = std::max(1ll, std::min({64ll, fit, (long long)((g.K + BK - 1) / BK)}));
+    long long best = -1;
+    for (long long sp = 1; sp <= smax; ++sp) {
+      const long long kc = (g.K + sp - 1) / sp;
+      const long long cost = ((tiles * sp + 151) / 152) * ((kc + BK - 1) / BK);
+      if (best < 0 || cost < best) {
+        best = cost;
+        splits = (int)sp;
+      }
+    }
+    kchunk = (g.K + splits - 1) / splits;
+    splits = (g.K + kchunk - 1) / kchunk;
+  } else {
+    if (work && tiles < target && g.K >= 8 * BK) {
+      long long want = (target + tiles - 1) / tiles;
+      long long maxs = g.K / (2 * BK);
+      long long fit = (long long)(work_elems / ((size_t)g.batch * g.M * g.N));
+      splits = (int)std::max<long long>(1, std::min(std::min(want, maxs), std::min(fit, (long long)64)));
+    }
+    kchunk = (g.K + splits - 1) / splits;
+    kchunk = ((kchunk + BK - 1) / BK) * BK;
+    splits = (g.K + kchunk - 1) / kchunk;
   }
-  int kchunk = (g.K + splits - 1) / splits;
-  kchunk = ((kchunk + BK - 1) / BK) * BK;
-  splits = (g.K + kchunk - 1) / kchunk;
   dim3 grid(tiles_n, tiles_m, (flat ? 1 : g.batch) * splits);
   TN_REQUIRE((flat ? 1 : g.batch) * (long long)splits < 65536 && tiles_m < 65536, "gemm: grid too large");
   {
