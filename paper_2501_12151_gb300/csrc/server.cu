@@ -125,7 +125,8 @@ size_t serve_estimate_bytes(const tnfem_grid& g, const tnfem_solve_opts& o) {
     else if (L <= 5) build = 18.4 * GiB;
     else build = (18.4 + 3.4 * (L - 5)) * GiB * (L >= 8 ? 1.5 : 1.0);
   }
-  return (size_t)(1.25 * std::max(sweep, build));
+  // + 128 MiB: a served 2D request (2^8, cap 16) held 174 MiB where a standalone solve held 57
+  return (size_t)(1.25 * std::max(sweep, build) + 128.0 * MiB);
 }
 
 }  // namespace tnfem
