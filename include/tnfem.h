@@ -261,12 +261,18 @@ tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_gr
 tnfem_status tnfem_energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u,
                                const tnfem_tt* v, double* out);
 
-/* a9's confirmation: the global relative residual ||f - A u||_2 / ||f||_2 in binary64, from the
- * explicitly formed residual train (A u by the MPO-TT product, ranks a_k r_k, then f - A u by
- * concatenation) whose norm is taken from the orthogonalised train, so it does not cancel.  Its
- * cost grows with (a r)^3 per core: intended for checks at small and moderate sizes. */
+/* a9's confirmation: the global relative residual ||f - A u||_2 / ||f||_2 in binary64, formed
+ * explicitly so that it does not cancel.  Grids with at most 2^22 unknowns (2D up to 2^10 x 2^10,
+ * 3D up to 2^6 per axis) whose dense expansion times the largest operator or train
+ * rank fits 2^28 doubles: u and f are expanded to dense device vectors and A u is formed densely,
+ * one operator core at a time (a batched GEMM per core; ~0.5 s at 2^10 x 2^10).  Larger grids: the
+ * residual train (A u by the MPO-TT product, ranks a_k r_k, then f - A u by concatenation) is
+ * orthogonalised and its norm read from the last core; its cost grows with (a r)^3 per core. */
 tnfem_status tnfem_residual_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u,
                                  double* out);
+/* The same quantity always by the orthogonalised residual train (the route of the larger grids). */
+tnfem_status tnfem_residual_norm_train(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u,
+                                       double* out);
 
 /* <x, y> and ||x|| (norm from the orthogonalised train). */
 tnfem_status tnfem_tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y, double* out);

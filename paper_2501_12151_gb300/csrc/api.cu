@@ -622,25 +622,52 @@ tnfem_status tnfem_tt_norm(tnfem_ctx* ctx, const tnfem_tt* x, double* out) {
   });
 }
 
+namespace {
+double residual_norm_train(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u) {
+  tnfem_tt* Au = mpo_apply(ctx, A, u);
+  tnfem_tt* r = nullptr;
+  double out = 0;
+  try {
+    r = tt_axpy(ctx, f, -1.0, Au);
+    const double rn = tt_norm(ctx, r);
+    const double fn = tt_norm(ctx, f);
+    out = fn > 0 ? rn / fn : rn;
+  } catch (...) {
+    tnfem_free_tt(Au);
+    tnfem_free_tt(r);
+    throw;
+  }
+  tnfem_free_tt(Au);
+  tnfem_free_tt(r);
+  return out;
+}
+
+void check_residual_args(const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u, const double* out) {
+  TN_REQUIRE(A && f && u && out, "null argument");
+  TN_REQUIRE(A->d == u->d && f->d == u->d, "operator, load and solution have different core counts");
+  for (int k = 0; k < u->d; ++k) TN_REQUIRE(A->n[k] == u->n[k] && f->n[k] == u->n[k], "modes differ");
+}
+}  // namespace
+
 tnfem_status tnfem_residual_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u,
                                  double* out) {
   if (!ctx) return TNFEM_E_INVALID;
   return guard(ctx, [&] {
-    TN_REQUIRE(A && f && u && out, "null argument");
-    tnfem_tt* Au = mpo_apply(ctx, A, u);
-    tnfem_tt* r = nullptr;
-    try {
-      r = tt_axpy(ctx, f, -1.0, Au);
-      const double rn = tt_norm(ctx, r);
-      const double fn = tt_norm(ctx, f);
-      *out = fn > 0 ? rn / fn : rn;
-    } catch (...) {
-      tnfem_free_tt(Au);
-      tnfem_free_tt(r);
-      throw;
-    }
-    tnfem_free_tt(Au);
-    tnfem_free_tt(r);
+    check_residual_args(A, f, u, out);
+    const size_t N = dense_elems(u);
+    size_t rk = 1;
+    for (int k = 0; k <= u->d; ++k) rk = std::max({rk, (size_t)A->a[k], (size_t)u->r[k], (size_t)f->r[k]});
+    if (N <= (1ull << 22) && N * rk <= (1ull << 28)) *out = residual_norm_dense(ctx, A, f, u);
+    else *out = residual_norm_train(ctx, A, f, u);
+  });
+}
+
+tnfem_status tnfem_residual_norm_train(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u,
+                                       double* out) {
+  if (!ctx) return TNFEM_E_INVALID;
+  return guard(ctx, [&] {
+    check_residual_args(A, f, u, out);
+    *out = residual_norm_train(ctx, A, f, u);
   });
 }
 

@@ -300,6 +300,10 @@ tnfem_tt* mpo_apply(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* x);
 double tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y);
 double tt_norm(tnfem_ctx* ctx, const tnfem_tt* x);
 double energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u, const tnfem_tt* v);
+// a9's global relative residual ||f - A u|| / ||f|| from dense expansions (tt_ops.cu); for grids
+// with at most 2^22 unknowns whose expansion times the largest rank fits 2^28 doubles
+size_t dense_elems(const tnfem_tt* x);
+double residual_norm_dense(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u);
 // MPO rounding (as a train with mode n^2)
 tnfem_mpo* mpo_round(tnfem_ctx* ctx, const tnfem_mpo* A, double eps, int rmax);
 

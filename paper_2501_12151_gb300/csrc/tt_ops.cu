@@ -521,4 +521,104 @@ double energy_norm(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* u, const 
   return out;
 }
 
+// ---- global residual on the dense expansion ---------------------------------------------------
+//
+// a9's confirmation ||f - A u||_2 / ||f||_2 for grids whose unknowns fit the device as a dense
+// vector (the 2^10 x 2^10 benchmark: 2.1M unknowns): u and f are expanded to dense vectors in the
+// QTT index order (i_0 most significant) by a chain of GEMMs, A u is formed densely by applying the
+// operator cores one at a time (a batched GEMM per core, intermediate [outputs so far][rank]
+// [inputs left]), and the residual is an explicit difference of dense vectors, so nothing cancels
+// beyond the rounding of A u itself.
+
+namespace {
+
+// out[((i * a1 + g) * a0 + a) * n + j] = in[((a * n + i) * n + j) * a1 + g]
+__global__ void mpo_core_perm_kernel(double* __restrict__ out, const double* __restrict__ in, int a0, int n, int a1) {
+  const long long total = (long long)a0 * n * n * a1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    const int g = (int)(r % a1);
+    r /= a1;
+    const int j = (int)(r % n);
+    r /= n;
+    const int i = (int)(r % n);
+    const int a = (int)(r / n);
+    out[(((long long)i * a1 + g) * a0 + a) * n + j] = in[t];
+  }
+}
+
+}  // namespace
+
+// dense expansion of a train into `out` (prod of modes entries); `tmp` holds as many
+size_t dense_elems(const tnfem_tt* x) {
+  size_t N = 1;
+  for (int k = 0; k < x->d; ++k) N *= (size_t)x->n[k];
+  return N;
+}
+
+void tt_full_device(tnfem_ctx* ctx, const tnfem_tt* x, double* out, double* tmp, size_t cap) {
+  // V_k [(o, i), r'] = V_{k-1} [o, r] . core_k [r, (i, r')]
+  double* cur = tmp;
+  double* nxt = out;
+  size_t rows = 1;
+  fill<double>(ctx, cur, 1.0, 1);
+  for (int k = 0; k < x->d; ++k) {
+    const int r0 = x->r[k], n = x->n[k], r1 = x->r[k + 1];
+    TN_REQUIRE(rows * n * r1 <= cap, "dense expansion: buffer too small");
+    GemmDesc g{(int)rows, n * r1, r0, 1, r0, 1, 0, (long long)n * r1, 1, 0, (long long)n * r1, 1, 0};
+    TN_REQUIRE(rows < (1ull << 31), "dense expansion: too many rows");
+    gemm<double>(ctx, g, 1.0, cur, x->core[k], 0.0, nxt);
+    rows *= n;
+    std::swap(cur, nxt);
+  }
+  if (cur != out) copy<double>(ctx, out, cur, rows);
+}
+
+double residual_norm_dense(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* f, const tnfem_tt* u) {
+  const int d = u->d;
+  const size_t N = dense_elems(u);
+  int amax = 1;
+  for (int k = 0; k <= d; ++k) amax = std::max(amax, A->a[k]);
+  int rmax = 1;
+  for (int k = 0; k <= d; ++k) rmax = std::max({rmax, u->r[k], f->r[k]});
+  const size_t cap = N * (size_t)std::max(amax, rmax);
+  DArr<double> X(ctx, cap), Y(ctx, cap), F(ctx, N);
+  tt_full_device(ctx, f, F.p, X.p, cap);
+  tt_full_device(ctx, u, Y.p, X.p, cap);  // u dense in Y
+  // state T [o][alpha][rest] in X / Y alternately: start with T = u (o = 1, alpha = 1, rest = N)
+  double* T = Y.p;
+  double* Tn = X.p;
+  size_t no = 1, rest = N;
+  for (int k = 0; k < d; ++k) {
+    const int a0 = A->a[k], n = A->n[k], a1 = A->a[k + 1];
+    DArr<double> Ap(ctx, (size_t)a0 * n * n * a1);
+    mpo_core_perm_kernel<<<std::max(1, std::min(1216, (int)((Ap.n + 255) / 256))), 256, 0, ctx->stream>>>(Ap.p, A->core[k],
+                                                                                                         a0, n, a1);
+    count_launch(ctx);
+    check_launch(ctx, "mpo_core_perm");
+    const size_t restn = rest / n;
+    if (no <= restn) {
+      // batch over the outputs o: T'[o][(i,b)][s] = Ap[(i,b)][(a,j)] . T[o][(a,j)][s]
+      TN_REQUIRE(no < 65536, "dense residual: batch too large");
+      GemmDesc g{n * a1, (int)restn, a0 * n, (int)no, (long long)a0 * n, 1, 0, (long long)restn, 1,
+                 (long long)a0 * n * restn, (long long)restn, 1, (long long)n * a1 * restn};
+      gemm<double>(ctx, g, 1.0, Ap.p, T, 0.0, Tn);
+    } else {
+      // batch over the remaining inputs s: rows o, T'[o][(i,b)][s] = T[o][(a,j)][s] . Ap^T
+      TN_REQUIRE(restn < 65536, "dense residual: batch too large");
+      GemmDesc g{(int)no, n * a1, a0 * n, (int)restn, (long long)a0 * n * restn, (long long)restn, 1, 1,
+                 (long long)a0 * n, 0, (long long)n * a1 * restn, (long long)restn, 1};
+      gemm<double>(ctx, g, 1.0, T, Ap.p, 0.0, Tn);
+    }
+    no *= n;
+    rest = restn;
+    std::swap(T, Tn);
+  }
+  // T = A u (a_d = 1, rest = 1), dense in the same order as F: r = F - A u
+  axpby<double>(ctx, T, 1.0, F.p, -1.0, N);  // T <- F - T
+  const double rn = nrm2<double>(ctx, T, N);
+  const double fn = nrm2<double>(ctx, F.p, N);
+  return fn > 0 ? rn / fn : rn;
+}
+
 }  // namespace tnfem

@@ -115,6 +115,7 @@ _sig("tnfem_energy_norm", _i, [_vp, _vp, _vp, _vp, _pd])
 _sig("tnfem_tt_dot", _i, [_vp, _vp, _vp, _pd])
 _sig("tnfem_tt_norm", _i, [_vp, _vp, _pd])
 _sig("tnfem_residual_norm", _i, [_vp, _vp, _vp, _vp, _pd])
+_sig("tnfem_residual_norm_train", _i, [_vp, _vp, _vp, _vp, _pd])
 _sig("tnfem_tt_round", _i, [_vp, _vp, _d, _i, _pvp])
 _sig("tnfem_tt_axpy", _i, [_vp, _vp, _d, _vp, _pvp])
 _sig("tnfem_mpo_apply", _i, [_vp, _vp, _vp, _pvp])
@@ -579,11 +580,13 @@ class Mpo:
         self.ctx.check(lib.tnfem_energy_norm(self.ctx.h, self.h, u.h, v.h if v else None, C.byref(out)))
         return out.value
 
-    def residual_norm(self, f: TT, u: TT) -> float:
-        """Relative residual ||f - A u||_2 / ||f||_2 of an approximate solution (step a9's check),
-        formed as an explicit train in binary64; cost grows with (a r)^3 per core."""
+    def residual_norm(self, f: TT, u: TT, route: str = "auto") -> float:
+        """Relative residual ||f - A u||_2 / ||f||_2 of an approximate solution (step a9's check) in
+        binary64: "auto" forms it on dense expansions where they fit (up to 2^22 unknowns), else as
+        an orthogonalised residual train; "train" always takes the train route."""
         out = C.c_double()
-        self.ctx.check(lib.tnfem_residual_norm(self.ctx.h, self.h, f.h, u.h, C.byref(out)))
+        fn = lib.tnfem_residual_norm_train if route == "train" else lib.tnfem_residual_norm
+        self.ctx.check(fn(self.ctx.h, self.h, f.h, u.h, C.byref(out)))
         return out.value
 
 

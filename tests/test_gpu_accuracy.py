@@ -76,6 +76,21 @@ def test_mixed_path_meets_1e6_at_benchmark_size(plate10):
     assert lib == pytest.approx(err, rel=1e-3), (lib, err)
 
 
+def test_global_residual_at_benchmark_size(plate10):
+    """Step a9's global confirmation at the benchmark size: ||f - A u|| / ||f|| of the mixed
+    solution through the library (dense expansions, A u formed densely on the device) against the
+    oracle's dense residual with its assembled sparse matrix; the two operators differ only by
+    the library's rounding of its train (1e-14 relative), so the values agree to 1e-3."""
+    P = plate10
+    u, info = P["ctx"].solve(P["A"], P["f"], P["pr"].opts)
+    got = P["A"].residual_norm(P["f"], u)
+    _, fv = fem.system(P["pr"].grid, P["pr"].material, P["pr"].loads)
+    ud = tt.to_natural_order(tt.tt_full(u.cores()), 2, 10)
+    want = np.linalg.norm(fv - P["Abc"] @ ud) / np.linalg.norm(fv)
+    assert 0 < want < 1e-3, want
+    assert got == pytest.approx(want, rel=1e-3), (got, want)
+
+
 def test_fp64_path_at_benchmark_size(plate10):
     P = plate10
     o = W.steel_plate_2d(levels=10, rank_cap=64, tol=1e-9, precision="fp64").opts

@@ -82,12 +82,13 @@ def test_fp64_solve_matches_galerkin(ctx, case):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed-local"])
-def test_global_residual_matches_dense(ctx, precision):
-    """Step a9's confirmation: the library's ||f - A u|| / ||f|| (explicit residual train, norm of
-    the orthogonalised train) against the dense residual of the oracle's assembled system, for a
-    converged solution (small residual: checked to 1e-4 relative, the rounding of a difference of
-    two trains of norm ~||f|| at ~1e-9 of it) and for trains far from the solution (checked to
-    1e-10)."""
+@pytest.mark.parametrize("route", ["auto", "train"])
+def test_global_residual_matches_dense(ctx, precision, route):
+    """Step a9's confirmation: the library's ||f - A u|| / ||f|| (route "auto": dense expansions
+    and a densely formed A u; route "train": explicit residual train, norm of the orthogonalised
+    train) against the dense residual of the oracle's assembled system, for a converged solution
+    (small residual: checked to 1e-4 relative, the rounding of a difference of two vectors of norm
+    ~||f|| at ~1e-9 of it) and for trains far from the solution (checked to 1e-10)."""
     pr = W.manufactured_2d(levels=5, rank_cap=64, tol=1e-10)
     pr.opts.precision = precision
     Abc, fv = fem.system(pr.grid, pr.material, pr.loads)
@@ -100,16 +101,16 @@ def test_global_residual_matches_dense(ctx, precision):
         un = tt.to_natural_order(tt.tt_full(cores), pr.grid.dim, pr.grid.levels)
         return np.linalg.norm(fv - Abc @ un) / np.linalg.norm(fv)
 
-    got, want = A.residual_norm(f, u), dense_rel(u.cores())
+    got, want = A.residual_norm(f, u, route), dense_rel(u.cores())
     assert 0 < want < 1e-6, want
     assert got == pytest.approx(want, rel=1e-4, abs=1e-13), (got, want)
     modes = W.qtt_modes(2, 5)
     for seed in (1, 2):
         cores = W.random_tt(seed, modes, [1] + [3] * (len(modes) - 1) + [1])
         x = ctx.tt_import(cores)
-        assert A.residual_norm(f, x) == pytest.approx(dense_rel(cores), rel=1e-10)
+        assert A.residual_norm(f, x, route) == pytest.approx(dense_rel(cores), rel=1e-10)
     zero = ctx.tt_import([np.zeros((1, m, 1)) for m in modes])
-    assert A.residual_norm(f, zero) == pytest.approx(1.0, rel=1e-13)
+    assert A.residual_norm(f, zero, route) == pytest.approx(1.0, rel=1e-13)
 
 
 def test_fp64_rank_capped_config_matches_oracle_amen(ctx):
