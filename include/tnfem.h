@@ -59,6 +59,12 @@ typedef struct {
   double lo[3], hi[3]; /* box corners; only the first dim entries are read */
   int clamped[6];      /* 1: homogeneous Dirichlet on all components of that face, 0: traction face */
   int plane_stress;    /* 2D only: 1 uses the modified Lame parameter lambda* = 2 lambda mu/(lambda+2 mu) */
+  int mapped;          /* 0: the box [lo, hi].  1: the parallelogram / parallelepiped
+                          {lo + sum_d xi_d edges[d] : xi in [0,1]^dim} (affine element maps, J
+                          constant, Section 5.1; hi unused); faces are the images of the unit box's
+                          faces; the material must be homogeneous (no E split inside the domain)
+                          and loads are gravity and uniform tractions only */
+  double edges[3][3];  /* mapped: edges[d] is the image of reference axis d (the columns of J) */
 } tnfem_grid;
 
 typedef struct {

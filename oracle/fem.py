@@ -14,7 +14,10 @@ What it computes, and where the paper defines it:
   chain rule grad phi = J^{-T} grad_xi phi (Eq. elassembly, Eq. grads), 2-point Gauss rules per
   axis (exact for the bilinear/trilinear integrands on parallelepipeds).
 * Grid: 2**levels equidistant nodes per axis including the boundary, (2**levels - 1)**D
-  elements, D * 2**(D*levels) unknowns (Section 5).
+  elements, D * 2**(D*levels) unknowns (Section 5).  The domain is a box, or the affine image of
+  the unit box (a parallelogram / parallelepiped, grid.edges): node i at lo + sum_d i_d/(n-1)
+  edges[d], every element the same parallelogram, the quadrature and the chain rule unchanged
+  (Section 5.1: J constant per element, exact for such maps).
 * Load f = M f0 from nodal values f0 (Section 5.3); a traction t on a face enters the same way
   through the face mass matrix (the paper only names Neumann sides).
 * Dirichlet faces: symmetric elimination A_bc = P A P + s (I - P), f_bc = P f, where P keeps the
@@ -149,11 +152,24 @@ def node_lin(idx: Sequence[np.ndarray], n: int) -> np.ndarray:
     return lin
 
 
+def node_coords(grid: Grid, idx: Sequence[np.ndarray]) -> np.ndarray:
+    """Physical coordinates (len, D) of the nodes with per-axis indices idx[d].  On a box the node
+    sits at lo + i h per axis; on a parallelogram / parallelepiped (grid.edges) at
+    lo + sum_d i_d / (n - 1) edges[d]."""
+    D = grid.dim
+    idx = [np.asarray(i).ravel() for i in idx]
+    if grid.edges is None:
+        ax = axis_coords(grid)
+        return np.stack([ax[d][idx[d]] for d in range(D)], axis=1)
+    E = np.asarray(grid.edges, dtype=float)[:D, :D]
+    xi = np.stack([i / (grid.n - 1) for i in idx], axis=1)
+    return np.asarray(grid.lo[:D], dtype=float)[None, :] + xi @ E
+
+
 def nodal_points(grid: Grid) -> np.ndarray:
     """Coordinates of all nodes in natural order, shape (n**D, D)."""
-    ax = axis_coords(grid)
-    mesh = np.meshgrid(*ax, indexing="ij")
-    return np.stack([m.ravel() for m in mesh], axis=1)
+    idx = np.meshgrid(*[np.arange(grid.n)] * grid.dim, indexing="ij")
+    return node_coords(grid, [m.ravel() for m in idx])
 
 
 def constrained_nodes(grid: Grid) -> np.ndarray:
@@ -181,24 +197,23 @@ def assemble(grid: Grid, mat: Material):
     D, n = grid.dim, grid.n
     N = n ** D
     ndof = D * N
-    ax = axis_coords(grid)
     corners = ref_corners(D)
     ne = n - 1
     el = np.meshgrid(*[np.arange(ne)] * D, indexing="ij")
     el = [e.ravel() for e in el]
     n_el = len(el[0])
-    # geometry is a tensor grid: per-axis spacing of element e along axis d
-    hs = [np.diff(a) for a in ax]
-    cx = ax[0][el[0]] + 0.5 * hs[0][el[0]]
+    # element corner coordinates relative to the element's first corner, and its centroid
+    Xc = [node_coords(grid, [el[d] + corners[a, d] for d in range(D)]) for a in range(1 << D)]
+    rel = np.stack([Xc[a] - Xc[0] for a in range(1 << D)], axis=1)      # (n_el, 2^D, D)
+    cx = np.mean([Xc[a][:, 0] for a in range(1 << D)], axis=0)
     Es = np.where(cx < mat.split_x, mat.E[0], mat.E[1])
-    geo = np.stack([np.round(hs[d][el[d]], 15) for d in range(D)] + [Es], axis=1)
+    geo = np.concatenate([np.round(rel.reshape(n_el, -1), 15), Es[:, None]], axis=1)
     uniq, inv = np.unique(geo, axis=0, return_inverse=True)
     inv = inv.ravel()
     Ks, Ms = [], []
     for u in uniq:
-        h = u[:D]
-        X = corners.astype(float) * h[None, :]
-        lam, mu = lame(u[D], mat.nu, D, grid.plane_stress)
+        X = u[:-1].reshape(1 << D, D)
+        lam, mu = lame(u[-1], mat.nu, D, grid.plane_stress)
         K, M = element_matrices(X, lam, mu)
         Ks.append(K)
         Ms.append(M)
@@ -232,7 +247,6 @@ def face_mass(grid: Grid, face: int) -> sp.csr_matrix:
     N = n ** D
     d, side = divmod(face, 2)
     fixed = 0 if side == 0 else n - 1
-    ax = axis_coords(grid)
     tang = [e for e in range(D) if e != d]
     fc = ref_corners(D - 1)
     ne = n - 1
@@ -249,8 +263,7 @@ def face_mass(grid: Grid, face: int) -> sp.csr_matrix:
         for t, e in enumerate(tang):
             full[e] = el[t] + fc[a, t]
         node_idx.append(node_lin(full, n))
-        for e in range(D):
-            Xs[:, a, e] = ax[e][full[e]]
+        Xs[:, a, :] = node_coords(grid, full)
     # group identical facet geometry
     rel = np.round(Xs - Xs[:, :1, :], 15).reshape(len(el[0]), -1)
     uniq, inv = np.unique(rel, axis=0, return_inverse=True)

@@ -57,7 +57,8 @@ void check_grid(const tnfem_grid* g) {
   TN_REQUIRE(g, "grid is null");
   TN_REQUIRE(g->dim == 2 || g->dim == 3, "grid.dim must be 2 or 3");
   TN_REQUIRE(g->levels >= 1 && g->levels <= 20, "grid.levels must be in [1, 20]");
-  for (int d = 0; d < g->dim; ++d) TN_REQUIRE(g->hi[d] > g->lo[d], "grid box is degenerate");
+  if (!g->mapped)
+    for (int d = 0; d < g->dim; ++d) TN_REQUIRE(g->hi[d] > g->lo[d], "grid box is degenerate");
 }
 
 void check_material(const tnfem_material* m) {
@@ -566,9 +567,12 @@ tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_gr
         for (int c = 0; c < D; ++c) qtt_index(D, L, c, &nodes[(size_t)q * D], &idx[((size_t)q * D + c) * u->d]);
       vals = eval_points(ctx, u, idx, (int)(n * nc * D));
     }
-    // gradient at the element centre: d N_a / d x_d = xi_{a,d} 2^{1-D} / h_d
+    // gradient at the element centre: d N_a / d x_d = xi_{a,d} 2^{1-D} / h_d on a box; on a mapped
+    // grid the same on the unit box (h = 1 / (N - 1)), then d/dx_e = sum_d Jinv[d][e] d/dxi_d
     std::vector<double> h(D);
-    for (int d = 0; d < D; ++d) h[d] = (grid->hi[d] - grid->lo[d]) / (N - 1);
+    for (int d = 0; d < D; ++d) h[d] = grid->mapped ? 1.0 / (N - 1) : (grid->hi[d] - grid->lo[d]) / (N - 1);
+    double Jinv[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    if (grid->mapped) grid_affine_inverse(*grid, Jinv, nullptr);
     const int ns = D == 2 ? 3 : 6;
     for (int64_t p = 0; p < n; ++p) {
       double gr[3][3] = {{0}};
@@ -580,6 +584,14 @@ tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_gr
             gr[c][d] += v * xi * std::pow(2.0, 1 - D) / h[d];
           }
         }
+      if (grid->mapped) {
+        double gp[3][3] = {{0}};
+        for (int c = 0; c < D; ++c)
+          for (int e = 0; e < D; ++e)
+            for (int d = 0; d < D; ++d) gp[c][e] += Jinv[d][e] * gr[c][d];
+        for (int c = 0; c < D; ++c)
+          for (int e = 0; e < D; ++e) gr[c][e] = gp[c][e];
+      }
       double* o = out + p * ns;
       if (D == 2) {
         o[0] = gr[0][0];

@@ -584,7 +584,97 @@ std::vector<SepTerm> stiffness_terms(int D, double lam, double mu) {
   return out;
 }
 
-HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* shift_out) {
+// Affine grids (grid.mapped): x = lo + J xi on the unit box, J[e][d] = edges[d][e].  The builders
+// run on the unit box and fold the map into the coefficients: physical derivatives are
+// d/dx_e = sum_p Jinv[p][e] d/dxi_p, and every integral carries |det J|.
+struct Affine {
+  double J[3][3] = {{0}}, Jinv[3][3] = {{0}}, det = 1.0;
+};
+
+static Affine affine_of(const tnfem_grid& g) {
+  Affine a;
+  const int D = g.dim;
+  for (int e = 0; e < D; ++e)
+    for (int d = 0; d < D; ++d) a.J[e][d] = g.edges[d][e];
+  if (D == 2) {
+    a.det = a.J[0][0] * a.J[1][1] - a.J[0][1] * a.J[1][0];
+    TN_REQUIRE(std::fabs(a.det) > 0, "mapped grid: the edges are linearly dependent");
+    a.Jinv[0][0] = a.J[1][1] / a.det;
+    a.Jinv[0][1] = -a.J[0][1] / a.det;
+    a.Jinv[1][0] = -a.J[1][0] / a.det;
+    a.Jinv[1][1] = a.J[0][0] / a.det;
+  } else {
+    const double(&m)[3][3] = a.J;
+    a.det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+            m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    TN_REQUIRE(std::fabs(a.det) > 0, "mapped grid: the edges are linearly dependent");
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        // cofactor of m[j][i] over det
+        const int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
+        a.Jinv[i][j] = (m[r0][c0] * m[r1][c1] - m[r0][c1] * m[r1][c0]) / a.det;
+      }
+  }
+  return a;
+}
+
+void grid_affine_inverse(const tnfem_grid& g, double Jinv[3][3], double* det) {
+  const Affine a = affine_of(g);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Jinv[i][j] = a.Jinv[i][j];
+  if (det) *det = a.det;
+}
+
+static tnfem_grid unit_box(const tnfem_grid& g) {
+  tnfem_grid u = g;
+  u.mapped = 0;
+  for (int d = 0; d < 3; ++d) {
+    u.lo[d] = 0.0;
+    u.hi[d] = 1.0;
+  }
+  return u;
+}
+
+// Stiffness terms of an affine grid on the unit box: block (c, c2) is
+// sum_{p,q} K[p][q] int d_p(test) d_q(trial) dxi with
+// K[p][q] = |det J| (lam Jinv[p][c] Jinv[q][c2] + mu Jinv[p][c2] Jinv[q][c] + mu [c = c2] sum_e Jinv[p][e] Jinv[q][e]);
+// the reference integral factors per axis: K where p = q = d, G^T on the test-derivative axis,
+// G on the trial-derivative axis, M elsewhere.
+static std::vector<SepTerm> stiffness_terms_mapped(int D, double lam, double mu, const Affine& af) {
+  std::vector<SepTerm> out;
+  for (int c = 0; c < D; ++c)
+    for (int c2 = 0; c2 < D; ++c2)
+      for (int p = 0; p < D; ++p)
+        for (int q = 0; q < D; ++q) {
+          double k = lam * af.Jinv[p][c] * af.Jinv[q][c2] + mu * af.Jinv[p][c2] * af.Jinv[q][c];
+          if (c == c2)
+            for (int e = 0; e < D; ++e) k += mu * af.Jinv[p][e] * af.Jinv[q][e];
+          k *= std::fabs(af.det);
+          if (k == 0.0) continue;
+          SepTerm t{c, c2, k, std::vector<int>(D)};
+          for (int d = 0; d < D; ++d) t.ops[d] = (d == p && d == q) ? OP_K : (d == p) ? OP_GT : (d == q) ? OP_G : OP_M;
+          out.push_back(t);
+        }
+  return out;
+}
+
+HTrain stiffness_train(const tnfem_grid& g_in, const tnfem_material& mat_in, double* shift_out) {
+  const bool mapped = g_in.mapped != 0;
+  Affine af;
+  tnfem_material mat = mat_in;
+  if (mapped) {
+    af = affine_of(g_in);
+    // the element weights of a two-material split are not separable on a sheared grid: the whole
+    // domain must lie on one side of the split (element centroids between xmin and xmax)
+    double xmin = g_in.lo[0], xmax = g_in.lo[0];
+    for (int d = 0; d < g_in.dim; ++d) (af.J[0][d] < 0 ? xmin : xmax) += af.J[0][d];
+    TN_REQUIRE(mat_in.E[0] == mat_in.E[1] || !(mat_in.split_x > xmin && mat_in.split_x <= xmax),
+               "mapped grid: the material must be homogeneous");
+    const double E = (mat_in.split_x > xmax) ? mat_in.E[0] : mat_in.E[1];
+    mat.E[0] = mat.E[1] = E;
+    mat.split_x = 1e300;
+  }
+  const tnfem_grid g = mapped ? unit_box(g_in) : g_in;
   const int D = g.dim, L = g.levels, n = 1 << L;
   double lam, mu;
   lame(mat.E[0], mat.nu, D, g.plane_stress != 0, lam, mu);
@@ -610,7 +700,7 @@ HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* s
     cats.push_back(f.get());
     axes.push_back(cats.back().joint);
   }
-  std::vector<SepTerm> terms = stiffness_terms(D, lam, mu);
+  std::vector<SepTerm> terms = mapped ? stiffness_terms_mapped(D, lam, mu, af) : stiffness_terms(D, lam, mu);
   // shift s: mean over components of the unconstrained diagonal at node (1,...,1); the
   // unconstrained entry (1,1) of each 1D matrix is kept in diag1 before projection for n > 2
   double s = 0;
@@ -651,7 +741,9 @@ HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* s
   return combine_axes(axes, terms, D, true);
 }
 
-HTrain mass_train(const tnfem_grid& g) {
+HTrain mass_train(const tnfem_grid& g_in) {
+  const double vol = g_in.mapped ? std::fabs(affine_of(g_in).det) : 1.0;
+  const tnfem_grid g = g_in.mapped ? unit_box(g_in) : g_in;
   const int D = g.dim, L = g.levels, n = 1 << L;
   std::vector<std::future<AxisOps>> cat_f;
   for (int d = 0; d < D; ++d)
@@ -661,7 +753,7 @@ HTrain mass_train(const tnfem_grid& g) {
   std::vector<HTrain> axes;
   for (auto& f : cat_f) axes.push_back(f.get().joint);
   std::vector<SepTerm> terms;
-  for (int c = 0; c < D; ++c) terms.push_back(SepTerm{c, c, 1.0, std::vector<int>(D, OP_M)});
+  for (int c = 0; c < D; ++c) terms.push_back(SepTerm{c, c, vol, std::vector<int>(D, OP_M)});
   return combine_axes(axes, terms, D, true);
 }
 
@@ -687,7 +779,27 @@ struct VecCatalog {
 
 }  // namespace
 
-HTrain load_train(const tnfem_grid& g, const tnfem_material& mat, const tnfem_load* loads, int n_loads) {
+HTrain load_train(const tnfem_grid& g_in, const tnfem_material& mat, const tnfem_load* loads, int n_loads) {
+  // affine grid: body forces carry |det J|, a traction on a face the ratio of the face's measure
+  // to the unit box face's (|J t| for the side along reference axis t in 2D, |J t1 x J t2| in 3D)
+  const bool mapped = g_in.mapped != 0;
+  Affine af;
+  if (mapped) af = affine_of(g_in);
+  auto face_scale = [&](int dn) {
+    if (!mapped) return 1.0;
+    double t[2][3] = {{0}};
+    int k = 0;
+    for (int d = 0; d < g_in.dim; ++d)
+      if (d != dn) {
+        for (int e = 0; e < 3; ++e) t[k][e] = e < g_in.dim ? af.J[e][d] : 0.0;
+        ++k;
+      }
+    if (g_in.dim == 2) return std::sqrt(t[0][0] * t[0][0] + t[0][1] * t[0][1]);
+    const double cx = t[0][1] * t[1][2] - t[0][2] * t[1][1], cy = t[0][2] * t[1][0] - t[0][0] * t[1][2],
+                 cz = t[0][0] * t[1][1] - t[0][1] * t[1][0];
+    return std::sqrt(cx * cx + cy * cy + cz * cz);
+  };
+  const tnfem_grid g = mapped ? unit_box(g_in) : g_in;
   const int D = g.dim, L = g.levels, n = 1 << L;
   std::vector<VecCatalog> cat(D);
   std::vector<std::vector<double>> X(D), P(D);
@@ -720,16 +832,19 @@ HTrain load_train(const tnfem_grid& g, const tnfem_material& mat, const tnfem_lo
     if (ld.kind == TNFEM_LOAD_GRAVITY) {
       std::vector<int> ops(D);
       for (int d = 0; d < D; ++d) ops[d] = massfn(d, [](double) { return 1.0; });
-      add(D - 1, -ld.rho * ld.g, ops);
+      add(D - 1, -ld.rho * ld.g * (mapped ? std::fabs(af.det) : 1.0), ops);
     } else if (ld.kind == TNFEM_LOAD_TRACTION) {
       TN_REQUIRE(ld.face >= 0 && ld.face < 2 * D, "traction face out of range");
       const int dn = ld.face / 2, side = ld.face % 2;
+      const double fs = face_scale(dn);
       for (int c = 0; c < D; ++c) {
         if (ld.traction[c] == 0.0) continue;
         std::vector<int> ops(D);
         for (int d = 0; d < D; ++d) ops[d] = (d == dn) ? endvec(d, side) : massfn(d, [](double) { return 1.0; });
-        add(c, ld.traction[c], ops);
+        add(c, ld.traction[c] * fs, ops);
       }
+    } else if (mapped) {
+      TN_REQUIRE(false, "mapped grid: loads must be gravity or uniform tractions");
     } else if (ld.kind == TNFEM_LOAD_FOURIER) {
       TN_REQUIRE(ld.n_modes >= 0 && (ld.n_modes == 0 || (ld.amp && ld.wave && ld.phase)), "fourier load arrays");
       for (int m = 0; m < ld.n_modes; ++m) {

@@ -32,7 +32,8 @@ class TnfemError(RuntimeError):
 
 class CGrid(C.Structure):
     _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("clamped", C.c_int * 6), ("plane_stress", C.c_int)]
+                ("clamped", C.c_int * 6), ("plane_stress", C.c_int), ("mapped", C.c_int),
+                ("edges", (C.c_double * 3) * 3)]
 
 
 class CMaterial(C.Structure):
@@ -168,6 +169,12 @@ def c_grid(g: Grid) -> CGrid:
     for f in range(6):
         cg.clamped[f] = 1 if (f < len(g.clamped) and g.clamped[f]) else 0
     cg.plane_stress = 1 if g.plane_stress else 0
+    edges = getattr(g, "edges", None)
+    cg.mapped = 1 if edges is not None else 0
+    if edges is not None:
+        for d in range(min(3, len(edges))):
+            for e in range(min(3, len(edges[d]))):
+                cg.edges[d][e] = float(edges[d][e])
     return cg
 
 

@@ -37,6 +37,9 @@ class Grid:
     hi: Sequence[float] = (1.0, 1.0, 1.0)
     clamped: Sequence[bool] = (True, False, False, False, False, False)
     plane_stress: bool = False
+    # parallelogram / parallelepiped domain {lo + sum_d xi_d edges[d] : xi in [0,1]^dim} when set
+    # (edges[d] is the image of reference axis d); `hi` is then unused
+    edges: Optional[Sequence[Sequence[float]]] = None
 
     @property
     def n(self) -> int:

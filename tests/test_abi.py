@@ -98,3 +98,43 @@ def test_host_builders_reject_bad_input():
         T.host_stiffness(g, W.Material(E=(1.0, 1.0), nu=0.5))
     with pytest.raises(T.TnfemError):
         T.host_load(g, W.Material(), [W.Load(kind="traction", face=5)])
+
+
+MAPPED = [(2, 3, ((1.5, 0.3), (0.6, 1.0)), (True, False, False, True, False, False)),
+          (2, 4, ((2.0, -0.5), (0.4, 1.0)), (True, True, False, False, False, False)),
+          (3, 2, ((1.2, 0.2, 0.1), (0.3, 0.9, 0.0), (0.1, 0.4, 0.8)), (True, False, False, False, False, True))]
+
+
+@pytest.mark.parametrize("dim,levels,edges,clamped", MAPPED)
+def test_host_builders_on_affine_domains_match_oracle(dim, levels, edges, clamped):
+    """Parallelogram / parallelepiped domains (affine element maps, Section 5.1): the host-built
+    operator (with its boundary-condition shift), mass operator and load equal the oracle's
+    element-loop matrices and load vector on the mapped nodes (permuted to the QTT order)."""
+    T = _lib()
+    g = W.Grid(dim=dim, levels=levels, lo=(0.2, -0.1, 0.3), edges=edges, clamped=clamped)
+    m = W.Material(E=(2.0, 2.0), nu=0.3)
+    cores, s = T.host_stiffness(g, m)
+    K, M = fem.assemble(g, m)
+    Aq = tt.matrix_to_qtt_order(fem.apply_bc(g, K), dim, levels)
+    assert np.abs(tt.mpo_full(cores) - Aq).max() <= 1e-12 * np.abs(Aq).max()
+    assert s == pytest.approx(fem.bc_shift(g, K), rel=1e-12)
+    Mq = tt.matrix_to_qtt_order(M, dim, levels)
+    assert np.abs(tt.mpo_full(T.host_mass(g)) - Mq).max() <= 1e-12 * np.abs(Mq).max()
+    loads = [W.Load(kind="gravity", rho=3.0)] + [
+        W.Load(kind="traction", face=f, traction=(0.5, -1.0, 0.2)) for f in range(2 * dim) if not clamped[f]]
+    fv = fem.load_vector(g, m, loads, M) * np.tile(~fem.constrained_nodes(g), dim)
+    fq = tt.to_qtt_order(fv, dim, levels)
+    assert np.abs(tt.tt_full(T.host_load(g, m, loads)) - fq).max() <= 1e-12 * np.abs(fq).max()
+
+
+def test_affine_domain_rejects_what_it_does_not_build():
+    """A two-material split inside a sheared domain and a Fourier load on it are refused."""
+    T = _lib()
+    g = W.Grid(dim=2, levels=3, edges=((1.0, 0.0), (0.5, 1.0)))
+    with pytest.raises(T.TnfemError):
+        T.host_stiffness(g, W.Material(E=(1.0, 2.0), split_x=0.7))
+    amp, wave, phase = W.fourier_modes(0, 2, 2)
+    with pytest.raises(T.TnfemError):
+        T.host_load(g, W.Material(), [W.Load(kind="fourier", amp=amp, wave=wave, phase=phase)])
+    # a split outside the domain is a homogeneous material
+    T.host_stiffness(g, W.Material(E=(1.0, 2.0), split_x=5.0))

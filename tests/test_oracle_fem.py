@@ -306,3 +306,62 @@ def test_multigrid_cg_matches_direct_solve(problem):
     ud = spla.spsolve(Abc.tocsc(), f)
     assert info["converged"] and info["iters"] < 100, info
     assert fem.energy_norm(Abc, u - ud) <= 1e-10 * fem.energy_norm(Abc, ud)
+
+
+SHEAR2 = ((1.5, 0.3), (0.6, 1.0))
+SHEAR3 = ((1.2, 0.2, 0.1), (0.3, 0.9, 0.0), (0.1, 0.4, 0.8))
+
+
+@pytest.mark.parametrize("dim,levels", [(2, 3), (3, 2)])
+def test_mapped_domain_rigid_modes_area_and_patch(dim, levels):
+    """Parallelogram / parallelepiped domains (the affine element maps of Section 5.1): the
+    free-free operator annihilates the rigid-body modes evaluated at the mapped node positions,
+    the mass matrix integrates 1 to |det J| (the domain's measure), and an affine displacement
+    field leaves zero residual at every interior node (patch test)."""
+    edges = SHEAR2 if dim == 2 else SHEAR3
+    g = W.Grid(dim=dim, levels=levels, lo=(0.2, -0.1, 0.3), edges=edges)
+    A, M = fem.assemble(g, W.Material(E=(2.0, 2.0), nu=0.3))
+    P = fem.nodal_points(g)
+    N = P.shape[0]
+    vol = abs(np.linalg.det(np.asarray(edges)))
+    e = np.zeros(dim * N)
+    e[:N] = 1.0
+    assert e @ (M @ e) == pytest.approx(vol, rel=1e-13)
+    modes = [np.eye(dim)[c][:, None] * np.ones(N)[None, :] for c in range(dim)]
+    for (a, b) in ([(0, 1)] if dim == 2 else [(0, 1), (0, 2), (1, 2)]):
+        r = np.zeros((dim, N))
+        r[a], r[b] = -P[:, b], P[:, a]
+        modes.append(r)
+    nA = abs(A).max()
+    for m in modes:
+        v = m.ravel()
+        assert np.abs(A @ v).max() <= 1e-12 * nA * np.abs(v).max()
+    # an affine field: only boundary rows feel it
+    G = np.arange(1, dim * dim + 1, dtype=float).reshape(dim, dim) / 7.0
+    v = (P @ G.T).T.ravel()
+    interior = np.all((np.indices((g.n,) * dim).reshape(dim, -1) > 0) &
+                      (np.indices((g.n,) * dim).reshape(dim, -1) < g.n - 1), axis=0)
+    res = (A @ v).reshape(dim, N)
+    assert np.abs(res[:, interior]).max() <= 1e-12 * nA * np.abs(v).max()
+
+
+def test_mapped_domain_with_axis_edges_equals_box():
+    """A parallelogram whose edges lie along the axes is the box: same matrices, same load."""
+    g_box = W.Grid(dim=2, levels=3, lo=(0.1, 0.2, 0.0), hi=(1.6, 0.9, 0.0))
+    g_map = W.Grid(dim=2, levels=3, lo=(0.1, 0.2, 0.0), edges=((1.5, 0.0), (0.0, 0.7)))
+    m = W.Material(E=(3.0, 3.0), nu=0.25)
+    loads = [W.Load(kind="gravity", rho=2.0), W.Load(kind="traction", face=1, traction=(0.5, -1.0, 0.0))]
+    (A1, M1), (A2, M2) = fem.assemble(g_box, m), fem.assemble(g_map, m)
+    assert abs(A1 - A2).max() <= 1e-13 * abs(A1).max()
+    assert abs(M1 - M2).max() <= 1e-15
+    np.testing.assert_allclose(fem.load_vector(g_box, m, loads), fem.load_vector(g_map, m, loads), rtol=0, atol=1e-14)
+
+
+def test_mapped_traction_resultant():
+    """A uniform traction on a side of a parallelogram sums to the traction times the side's length."""
+    g = W.Grid(dim=2, levels=3, lo=(0.0, 0.0, 0.0), edges=SHEAR2)
+    N = g.n ** 2
+    for face in range(4):
+        f = fem.load_vector(g, W.Material(), [W.Load(kind="traction", face=face, traction=(2.0, -3.0, 0.0))])
+        length = np.linalg.norm(SHEAR2[1 - face // 2])       # the side runs along the other edge
+        np.testing.assert_allclose([f[:N].sum(), f[N:].sum()], [2.0 * length, -3.0 * length], rtol=1e-12)
