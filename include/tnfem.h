@@ -462,6 +462,12 @@ tnfem_status tnfem_wait(tnfem_server* s, uint64_t id, int64_t timeout_us, tnfem_
 /* Copy a finished request's solution cores (out->result_doubles doubles, cores in train order,
  * layout of tnfem_tt_export; cores may be NULL to discard) and forget the request. */
 tnfem_status tnfem_result_take(tnfem_server* s, uint64_t id, double* cores);
+/* Cancel a request that is still queued: it ends at once with status TNFEM_E_INVALID ("cancelled
+ * before admission"); TNFEM_E_INVALID when it is unknown, already running or done. */
+tnfem_status tnfem_cancel(tnfem_server* s, uint64_t id);
+/* Requests waiting for admission, requests running, and the sum of the running requests' memory
+ * estimates (any output pointer may be NULL). */
+tnfem_status tnfem_server_stats(tnfem_server* s, int* queued, int* running, size_t* admitted_bytes);
 /* Stop: requests already admitted finish, queued ones end with TNFEM_E_INVALID; joins the workers
  * and frees the server. */
 tnfem_status tnfem_server_stop(tnfem_server* s);

@@ -22,6 +22,8 @@
 #include <cmath>
 #include <memory>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "amen.h"
 #include "cg_fused.h"
 #include "internal.h"
@@ -303,6 +305,9 @@ struct ChunkGraph {
 template <typename T>
 class Amen {
  public:
+  ~Amen() {
+    if (nvtx_open_) nvtxRangePop();  // a solve that ended by an exception mid-phase
+  }
   Amen(tnfem_ctx* ctx, const tnfem_mpo* A, const std::vector<AmenSource>& src, const AmenParams& prm,
        const tnfem_tt* x0)
       : ctx_(ctx), A_(A), src_(src), prm_(prm) {
@@ -410,6 +415,13 @@ class Amen {
   std::chrono::steady_clock::time_point phase_t0_;
   double phase_ms_[kPhases] = {};
   void phase(int next) {
+    // NVTX ranges name the phases for a profiler (ncu --nvtx); no cost when no tool is attached
+    static const char* const kNames[kPhases] = {"tnfem rhs projection", "tnfem local residual", "tnfem local solve",
+                                                "tnfem truncated svd", "tnfem enrichment", "tnfem environments",
+                                                "tnfem other"};
+    if (nvtx_open_) nvtxRangePop();
+    nvtx_open_ = next >= 0;
+    if (nvtx_open_) nvtxRangePushA(kNames[next]);
     if (!trace_) return;
     sync(ctx_);
     const auto now = std::chrono::steady_clock::now();
@@ -417,6 +429,7 @@ class Amen {
     cur_phase_ = next;
     phase_t0_ = now;
   }
+  bool nvtx_open_ = false;           // an NVTX phase range is open
   long long fallbacks_ = 0;          // binary32 local solves finished in binary64
   double init_rn_ = 0.0;
   ChunkGraph graph_[2];  // conjugate-gradient chunk graphs, binary32 / binary64

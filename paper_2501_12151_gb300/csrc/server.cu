@@ -371,6 +371,32 @@ tnfem_status tnfem_result_take(tnfem_server* s, uint64_t id, double* cores) {
   return TNFEM_OK;
 }
 
+tnfem_status tnfem_cancel(tnfem_server* s, uint64_t id) {
+  if (!s) return TNFEM_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return TNFEM_E_INVALID;
+  Request* r = it->second.get();
+  auto q = std::find(s->queue.begin(), s->queue.end(), r);
+  if (q == s->queue.end()) return TNFEM_E_INVALID;  // already running or done
+  s->queue.erase(q);
+  r->status = TNFEM_E_INVALID;
+  r->err = "cancelled before admission";
+  r->t_start = r->t_end = now_us();
+  r->done = true;
+  s->cv_done.notify_all();
+  return TNFEM_OK;
+}
+
+tnfem_status tnfem_server_stats(tnfem_server* s, int* queued, int* running, size_t* admitted_bytes) {
+  if (!s) return TNFEM_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (queued) *queued = (int)s->queue.size();
+  if (running) *running = s->running;
+  if (admitted_bytes) *admitted_bytes = s->admitted_bytes;
+  return TNFEM_OK;
+}
+
 tnfem_status tnfem_server_stop(tnfem_server* s) {
   if (!s) return TNFEM_E_INVALID;
   {

@@ -150,6 +150,8 @@ _sig("tnfem_submit", _i, [_vp, C.POINTER(CGrid), C.POINTER(CMaterial), C.POINTER
 _sig("tnfem_wait", _i, [_vp, C.c_uint64, C.c_int64, C.POINTER(CRequestInfo)])
 _sig("tnfem_result_take", _i, [_vp, C.c_uint64, _pd])
 _sig("tnfem_server_stop", _i, [_vp])
+_sig("tnfem_cancel", _i, [_vp, C.c_uint64])
+_sig("tnfem_server_stats", _i, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)])
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed-local": 2, "mixed-tf32": 3}
 PROF_CLASSES = {"contract32": 0, "contract64": 1, "krylov": 2, "qr": 3, "svd": 4, "other": 5, "cg32": 6, "cg64": 7}
@@ -652,6 +654,15 @@ class Server:
                     cores.append(buf[off:off + sz].reshape(shp).copy())
                     off += sz
         return cores, d
+
+    def cancel(self, rid: int) -> bool:
+        """Cancel a queued request; False when it was already admitted (or done)."""
+        return lib.tnfem_cancel(self.h, rid) == 0
+
+    def stats(self) -> dict:
+        q, r, b = C.c_int(), C.c_int(), C.c_size_t()
+        _check(lib.tnfem_server_stats(self.h, C.byref(q), C.byref(r), C.byref(b)))
+        return {"queued": q.value, "running": r.value, "admitted_bytes": b.value}
 
     def stop(self):
         if getattr(self, "h", None):

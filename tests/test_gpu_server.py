@@ -97,6 +97,27 @@ def test_admission_keeps_estimates_within_budget(tn):
     assert starts == sorted(starts)
 
 
+def test_cancel_queued_request_and_stats(tn):
+    """A request still waiting for admission can be cancelled (a host-side fault injection of
+    SURVEY's "cancelled request"); the running one is not affected, and the queue statistics
+    count what waits and what runs."""
+    pr = W.steel_plate_2d(levels=8, rank_cap=64, tol=1e-9, precision="mixed-local")
+    srv = tn.Server(0, workers=1)
+    ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for _ in range(3)]
+    st = srv.stats()
+    assert st["queued"] + st["running"] == 3 and st["running"] <= 1
+    assert srv.cancel(ids[2])
+    assert not srv.cancel(ids[2])                          # already done (cancelled)
+    _, info = srv.wait(ids[2], take=False)
+    assert info["status"] == "INVALID" and "cancelled" in info["message"]
+    first = srv.wait(ids[0], take=False)[1]
+    assert first["status"] in ("OK", "NOT_CONVERGED")
+    assert not srv.cancel(ids[0])                          # finished: nothing to cancel
+    srv.wait(ids[1], take=False)
+    assert srv.stats() == {"queued": 0, "running": 0, "admitted_bytes": 0}
+    srv.stop()
+
+
 def test_wait_timeout_and_stop_with_queued_requests(tn):
     pr = W.steel_plate_2d(levels=8, rank_cap=64, tol=1e-9, precision="mixed-local")
     srv = tn.Server(0, workers=1)

@@ -309,3 +309,27 @@ def test_affine_domain_solve_matches_galerkin(ctx, dim, levels, edges):
         want = [eps[0, 0], eps[1, 1], eps[0, 1]] if dim == 2 else \
             [eps[0, 0], eps[1, 1], eps[2, 2], eps[1, 2], eps[0, 2], eps[0, 1]]
         np.testing.assert_allclose(got[p], want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+
+
+def test_checkpoint_and_resume(ctx):
+    """Checkpoint / resume: a solve stopped after three sweeps is exported to host memory, imported
+    into a fresh context and resumed as the start guess; the resumed solve reaches the Galerkin
+    solution like an uninterrupted one, in no more sweeps than the uninterrupted solve (the
+    enrichment train and the environments are rebuilt on resume)."""
+    from paper_2501_12151_gb300 import tnfem
+    pr = W.steel_plate_2d(levels=6, rank_cap=64, tol=1e-10, precision="fp64")
+    Abc, uh = _galerkin(pr)
+    A = ctx.stiffness(pr.grid, pr.material)
+    f = ctx.load(pr.grid, pr.material, pr.loads)
+    full, info_full = ctx.solve(A, f, pr.opts)
+    o = W.SolveOpts(**{**pr.opts.__dict__, "max_sweeps": 3})
+    part, info_part = ctx.solve(A, f, o)
+    assert info_part["status"] == "NOT_CONVERGED" and info_part["sweeps"] == 3
+    saved = part.cores()                               # host checkpoint
+    ctx2 = tnfem.Context(0)
+    A2 = ctx2.stiffness(pr.grid, pr.material)
+    f2 = ctx2.load(pr.grid, pr.material, pr.loads)
+    u, info = ctx2.solve(A2, f2, pr.opts, x0=ctx2.tt_import(saved))
+    err = _energy_err(Abc, tt.tt_full(u.cores()), uh, pr.grid)
+    assert info["converged"] == 1 and err <= 1e-8, (err, info)
+    assert info["sweeps"] <= info_full["sweeps"] + 1, (info["sweeps"], info_full["sweeps"])
