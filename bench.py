@@ -258,6 +258,17 @@ def rel_energy_err(A, u, uh, nh):
     return A.energy_norm(u, uh) / nh
 
 
+# DRAM bytes per launch of the two classes that can be the largest, from single-kernel ncu
+# captures at the 2^10 x 2^10 working shape (profiles/): the three binary64 GEMM stages of one local
+# matvec read 1.16 / 4.49 / 5.15 MB and write nothing (operands L2-resident; mean 3.6 MB); the
+# fused CG moves ~0.19 MB per pass, and a launch of the solve runs ~19 passes on average
+# (3.3k CG steps in 173 launches), so ~3.6 MB per launch (scaled by passes from the 51-pass capture).
+TRAFFIC_NCU = {"contract64": 3.6e6, "cg32": 3.6e6}
+TRAFFIC_NOTE = {"contract64": "ncu dram__bytes_read+write, mean of the 3 stage launches of one binary64 local matvec at "
+                              "the working shape (profiles/gemm_kernel_double_local_matvec_steel2d_L10.md)",
+                "cg32": "ncu DRAM bytes of a 51-pass fused-CG launch at the working shape scaled to the solve's mean "
+                        "of ~19 passes per launch (profiles/fcg_kernel_steel2d_L10.md)"}
+
 PROF_KERNEL = {"contract32": "gemm_kernel<float>", "contract64": "gemm_kernel<double>",
                "krylov": "CG vector kernels", "qr": "qr_*_kernel (Householder QR)",
                "svd": "svd_*_kernel (one-sided Jacobi SVD)", "other": "other kernels",
@@ -320,7 +331,12 @@ def run_ours(args):
     # a9's global confirmation of the last timed solution: ||f - A u|| / ||f|| in binary64 (dense
     # expansion where it fits the device, else the orthogonalised residual train); untimed
     t_res = time.perf_counter()
-    global_res = A.residual_norm(f, u) if args.global_residual else None
+    global_res = None
+    if args.global_residual:
+        try:
+            global_res = A.residual_norm(f, u)
+        except tnfem.TnfemError as e:  # beyond the dense route the residual train may not fit
+            global_res = f"not formed: {e}"
     t_res = time.perf_counter() - t_res
 
     # end to end through the public API: host parameters -> build -> solve -> cores to host
@@ -421,8 +437,12 @@ def run_ours(args):
                     "tflops": (prof[c]["flops"] / (prof[c]["ms"] * 1e-3) * 1e-12) if prof[c]["ms"] > 0 else None}
                 for c in prof}
     measured_fma = {"fp64": ctx.fma_peak("fp64"), "fp32": ctx.fma_peak("fp32")}
+    traffic = args.traffic if args.traffic is not None else (
+        TRAFFIC_NCU.get(cls) if PROBLEM["name"] == "steel2d" and not df_route else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": args.traffic,
+                "frac": achieved / peak if peak else None, "traffic": traffic,
+                "traffic_source": (TRAFFIC_NOTE.get(cls) if traffic is not None and args.traffic is None else
+                                   ("--traffic" if traffic is not None else None)),
                 "kernel": PROF_KERNEL[cls], "class": cls,
                 "peak_source": peak_note,
                 "fma_peak_measured_tflops": measured_fma,
@@ -466,7 +486,7 @@ def run_ours(args):
                      "reference": "Galerkin solution u_h of the oracle (element-loop assembly, V-cycle CG), "
                                   "stored as a QTT train accurate to 1e-10 in energy norm",
                      "global_rel_residual": global_res,
-                     "global_residual_s": t_res if global_res is not None else None,
+                     "global_residual_s": t_res if isinstance(global_res, float) else None,
                      "sweeps": last["sweeps"], "max_rank": last["max_rank"], "local_iters": last["local_iters"],
                      "converged": bool(last["converged"])},
         "gpu_launches": launches,

@@ -734,7 +734,7 @@ void Amen<T>::source_proj(int k, bool zl, bool zr, double* out, int ry0, int ry1
 template <typename T>
 template <typename U>
 bool Amen<T>::setup_pre(int r0, int n, int r1, int a0, int a1, const U* PL, const U* Ak, const U* PR, DArr<U>& work) {
-  if (!prm_.precond || !bj_fits(r0, n, r1)) return false;
+  if (!prm_.precond || !bj_fits(r0, n, r1) || !bj_worth_it(r0, n)) return false;
   work.ensure(ctx_, bj_work_elems(r0, n, r1, a0, a1));
   bjP_.ensure(ctx_, (size_t)r1 * r0 * n * r0 * n);
   const bool ok = bj_setup<U>(ctx_, r0, n, r1, a0, a1, PL, Ak, PR, bjP_.p, work.p, work.n, ctl_.p + 2);

@@ -168,6 +168,11 @@ bool bj_fits(int r0, int n, int r1) {
   return m <= kBlockJacobiMaxM && (long long)r1 * m * m <= kBlockJacobiMaxElems;
 }
 
+bool bj_worth_it(int r0, int n) {
+  const size_t m = (size_t)r0 * n;
+  return (m * m + 2 * m) * sizeof(float) <= kInvertSmemMax || m <= 512;
+}
+
 size_t bj_work_elems(int r0, int n, int r1, int a0, int a1) {
   const size_t m = (size_t)r0 * n;
   const size_t t1 = (size_t)a0 * n * n * r1;

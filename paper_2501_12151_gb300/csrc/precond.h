@@ -11,6 +11,11 @@ constexpr long long kBlockJacobiMaxM = 1024;
 constexpr long long kBlockJacobiMaxElems = 64ll << 20;
 
 bool bj_fits(int r0, int n, int r1);
+// Whether the sweep preconditions a local system with blocks of m = r0 n rows: always when a block
+// is inverted in one CTA's shared memory (m up to ~234), and from global memory up to m = 512.
+// Beyond (the 3D configuration: m = 768) the set-up cost more than the iterations it saved (2^7
+// cube, rank cap 96: 15.2 s with the preconditioner, 11.9 s with plain CG, measured).
+bool bj_worth_it(int r0, int n);
 // Workspace (precision T elements) of bj_setup.
 size_t bj_work_elems(int r0, int n, int r1, int a0, int a1);
 // Build the inverses of the r1 diagonal blocks into Pinv ([r1][r0 n][r0 n] binary32).  Ap is the

@@ -353,7 +353,7 @@ tnfem_status tnfem_wait(tnfem_server* s, uint64_t id, int64_t timeout_us, tnfem_
     out->peak_bytes = r->peak_bytes;
     out->ncores = (int)r->modes.size();
     for (int k = 0; k < out->ncores && k < 63; ++k) out->modes[k] = r->modes[k];
-    for (int k = 0; k <= out->ncores && k < 64; ++k) out->ranks[k] = r->ranks[k];
+    for (int k = 0; k < (int)r->ranks.size() && k < 64; ++k) out->ranks[k] = r->ranks[k];
     out->result_doubles = r->cores.size();
     snprintf(out->message, sizeof(out->message), "%s", r->err.c_str());
   }
