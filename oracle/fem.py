@@ -17,7 +17,11 @@ What it computes, and where the paper defines it:
   elements, D * 2**(D*levels) unknowns (Section 5).  The domain is a box, or the affine image of
   the unit box (a parallelogram / parallelepiped, grid.edges): node i at lo + sum_d i_d/(n-1)
   edges[d], every element the same parallelogram, the quadrature and the chain rule unchanged
-  (Section 5.1: J constant per element, exact for such maps).
+  (Section 5.1: J constant per element, exact for such maps).  Or a general convex
+  quadrilateral (2D, grid.quad: corners P0..P3, the bilinear map of the unit square): node
+  (i, j) at the bilinear map of (i/(n-1), j/(n-1)); assembled either exactly (J at every
+  quadrature point) or, as Algorithm 1 does, with each element's J and det J frozen at the
+  element centre xi = 0 (``frozen_jacobian``).
 * Load f = M f0 from nodal values f0 (Section 5.3); a traction t on a face enters the same way
   through the face mass matrix (the paper only names Neumann sides).
 * Dirichlet faces: symmetric elimination A_bc = P A P + s (I - P), f_bc = P f, where P keeps the
@@ -84,21 +88,24 @@ def gauss(dim: int):
     return pts, w
 
 
-def element_matrices(X: np.ndarray, lam: float, mu: float):
+def element_matrices(X: np.ndarray, lam: float, mu: float, frozen: bool = False):
     """Element stiffness and mass for corner coordinates X (2^D, D) (Eq. elassembly).
 
     Local unknown (a, c) sits at a*D + c.  Stiffness entry for test (a,c), trial (b,c'):
       int lam d_c N_a d_c' N_b + mu delta_cc' grad N_a . grad N_b + mu d_c' N_a d_c N_b
-    which is sigma(N_b e_c') : eps(N_a e_c) written out.
+    which is sigma(N_b e_c') : eps(N_a e_c) written out.  With `frozen` the Jacobian is taken at
+    the element centre xi = 0 for every quadrature point, as Algorithm 1 does (exact for
+    parallelograms, an approximation on general quadrilaterals).
     """
     dim = X.shape[1]
     nb = 1 << dim
     K = np.zeros((nb * dim, nb * dim))
     M = np.zeros((nb * dim, nb * dim))
     pts, w = gauss(dim)
+    J0 = X.T @ shape(dim, np.zeros(dim))[1]
     for q in range(len(pts)):
         N, dN = shape(dim, pts[q])
-        J = X.T @ dN                           # J[d, e] = dx_d / dxi_e
+        J = J0 if frozen else X.T @ dN         # J[d, e] = dx_d / dxi_e
         detJ = np.linalg.det(J)
         G = dN @ np.linalg.inv(J)              # rows: grad_x N_a = J^{-T} grad_xi N_a
         wq = w[q] * abs(detJ)
@@ -158,6 +165,12 @@ def node_coords(grid: Grid, idx: Sequence[np.ndarray]) -> np.ndarray:
     lo + sum_d i_d / (n - 1) edges[d]."""
     D = grid.dim
     idx = [np.asarray(i).ravel() for i in idx]
+    if getattr(grid, "quad", None) is not None:
+        # bilinear map of the unit square onto the quadrilateral P0 P1 P2 P3 (Section 5.1)
+        P = np.asarray(grid.quad, dtype=float)
+        xi, eta = idx[0] / (grid.n - 1), idx[1] / (grid.n - 1)
+        return (np.outer((1 - xi) * (1 - eta), P[0]) + np.outer(xi * (1 - eta), P[1]) +
+                np.outer((1 - xi) * eta, P[2]) + np.outer(xi * eta, P[3]))
     if grid.edges is None:
         ax = axis_coords(grid)
         return np.stack([ax[d][idx[d]] for d in range(D)], axis=1)
@@ -188,11 +201,13 @@ def constrained_nodes(grid: Grid) -> np.ndarray:
 # assembly (element loop, Section 3)
 # ---------------------------------------------------------------------------------------
 
-def assemble(grid: Grid, mat: Material):
+def assemble(grid: Grid, mat: Material, frozen_jacobian: bool = False):
     """Free-free stiffness A and mass M (CSR, natural ordering) by an element loop.
 
     Element matrices are computed per element from its corner coordinates; identical
-    elements (same geometry and Young's modulus) reuse one computed matrix.
+    elements (same geometry and Young's modulus) reuse one computed matrix.  `frozen_jacobian`
+    takes each element's Jacobian at its centre (Algorithm 1's assembly for general
+    quadrilaterals).
     """
     D, n = grid.dim, grid.n
     N = n ** D
@@ -214,7 +229,7 @@ def assemble(grid: Grid, mat: Material):
     for u in uniq:
         X = u[:-1].reshape(1 << D, D)
         lam, mu = lame(u[-1], mat.nu, D, grid.plane_stress)
-        K, M = element_matrices(X, lam, mu)
+        K, M = element_matrices(X, lam, mu, frozen_jacobian)
         Ks.append(K)
         Ms.append(M)
     Ks = np.array(Ks)
@@ -411,9 +426,9 @@ def apply_bc(grid: Grid, A: sp.csr_matrix, f: np.ndarray = None):
     return Abc, free * f
 
 
-def system(grid: Grid, mat: Material, loads: Sequence[Load]):
+def system(grid: Grid, mat: Material, loads: Sequence[Load], frozen_jacobian: bool = False):
     """Boundary-condition-applied Galerkin system (A_bc, f_bc) in natural ordering."""
-    A, M = assemble(grid, mat)
+    A, M = assemble(grid, mat, frozen_jacobian)
     f = load_vector(grid, mat, loads, M)
     return apply_bc(grid, A, f)
 

@@ -40,6 +40,9 @@ class Grid:
     # parallelogram / parallelepiped domain {lo + sum_d xi_d edges[d] : xi in [0,1]^dim} when set
     # (edges[d] is the image of reference axis d); `hi` is then unused
     edges: Optional[Sequence[Sequence[float]]] = None
+    # 2D general quadrilateral when set: corners (P0, P1, P2, P3) at reference (0,0), (1,0), (0,1),
+    # (1,1), the bilinear map of the unit square; `lo`, `hi` and `edges` are then unused
+    quad: Optional[Sequence[Sequence[float]]] = None
 
     @property
     def n(self) -> int:

@@ -365,3 +365,83 @@ def test_mapped_traction_resultant():
         f = fem.load_vector(g, W.Material(), [W.Load(kind="traction", face=face, traction=(2.0, -3.0, 0.0))])
         length = np.linalg.norm(SHEAR2[1 - face // 2])       # the side runs along the other edge
         np.testing.assert_allclose([f[:N].sum(), f[N:].sum()], [2.0 * length, -3.0 * length], rtol=1e-12)
+
+
+QUAD = ((0.0, 0.0), (1.0, 0.1), (0.2, 0.9), (1.3, 1.4))   # convex, not a parallelogram
+
+
+def _shoelace(P):
+    ring = [P[0], P[1], P[3], P[2]]
+    return 0.5 * abs(sum(ring[i][0] * ring[i - 3][1] - ring[i - 3][0] * ring[i][1] for i in range(4)))
+
+
+def test_quad_grid_on_a_parallelogram_is_the_affine_grid():
+    """Corners with P3 = P1 + P2 - P0 make the bilinear map affine: the frozen-Jacobian assembly
+    (Algorithm 1) then coincides with the exact affine assembly, node positions, matrices and
+    loads alike."""
+    P0, e0, e1 = np.array([0.2, -0.1]), np.array([1.5, 0.3]), np.array([0.6, 1.0])
+    quad = (P0, P0 + e0, P0 + e1, P0 + e0 + e1)
+    g_aff = W.Grid(dim=2, levels=3, lo=(0.2, -0.1, 0.0), edges=(e0, e1), clamped=(False, False, True, False))
+    g_quad = W.Grid(dim=2, levels=3, quad=quad, clamped=(False, False, True, False))
+    m = W.Material(E=(3.0, 3.0), nu=0.25)
+    loads = [W.Load(kind="gravity", rho=2.0), W.Load(kind="traction", face=1, traction=(0.5, -1.0, 0.0))]
+    np.testing.assert_allclose(fem.nodal_points(g_quad), fem.nodal_points(g_aff), rtol=0, atol=1e-15)
+    (A1, M1), (A2, M2) = fem.assemble(g_aff, m), fem.assemble(g_quad, m, frozen_jacobian=True)
+    assert abs(A1 - A2).max() <= 1e-13 * abs(A1).max()
+    assert abs(M1 - M2).max() <= 1e-15
+    A1b, f1 = fem.system(g_aff, m, loads)
+    A2b, f2 = fem.system(g_quad, m, loads, frozen_jacobian=True)
+    assert abs(A1b - A2b).max() <= 1e-13 * abs(A1b).max()
+    np.testing.assert_allclose(f1, f2, rtol=0, atol=1e-14)
+
+
+def test_frozen_element_matrix_is_that_of_the_centre_parallelogram():
+    """Freezing the Jacobian at the element centre (Algorithm 1 evaluates J at xi = 0 of
+    Q = [-1,1]^2) gives the exact matrices of the parallelogram x = x_c + J(0) xi spanned by the
+    centre Jacobian: built here from the exact path on that other geometry."""
+    R = 2.0 * fem.ref_corners(2) - 1.0                             # corner signs in [-1,1]^2
+    at = {(-1, -1): (0.0, 0.0), (1, -1): (1.1, 0.2), (-1, 1): (0.3, 0.8), (1, 1): (1.6, 1.5)}
+    X = np.array([at[(int(r[0]), int(r[1]))] for r in R])
+    xc = X.mean(axis=0)
+    J0 = X.T @ R / 4.0                                             # dx_d / dxi_e at xi = 0
+    Xp = xc[None, :] + R @ J0.T
+    Kf, Mf = fem.element_matrices(X, 1.7, 0.9, frozen=True)
+    Kp, Mp = fem.element_matrices(Xp, 1.7, 0.9)
+    np.testing.assert_allclose(Kf, Kp, rtol=0, atol=1e-14 * abs(Kp).max())
+    np.testing.assert_allclose(Mf, Mp, rtol=0, atol=1e-15)
+    Ke, _ = fem.element_matrices(X, 1.7, 0.9)
+    assert abs(Ke - Kf).max() > 1e-3 * abs(Ke).max()             # the quadrilateral is not affine
+
+
+def test_quad_frozen_assembly_area_translations_and_convergence():
+    """General quadrilateral, Jacobian frozen per element: the mass integrates 1 to the exact area
+    (det J is affine in xi, so the centre value is its element mean), translations are in the
+    kernel, the rotation's energy and the distance to the exactly assembled Galerkin solution
+    fall like h^2 (the frozen Jacobian is an O(h) relative perturbation of the element map's)."""
+    m = W.Material(E=(2.0, 2.0), nu=0.3)
+    loads = [W.Load(kind="gravity", rho=1.0), W.Load(kind="traction", face=1, traction=(0.0, -0.5, 0.0))]
+    rot_energy, sol_diff = [], []
+    for levels in (3, 4, 5):
+        g = W.Grid(dim=2, levels=levels, quad=QUAD, clamped=(True, False, False, False))
+        A, M = fem.assemble(g, m, frozen_jacobian=True)
+        N = g.n ** 2
+        P = fem.nodal_points(g)
+        one = np.concatenate([np.ones(N), np.zeros(N)])
+        assert one @ (M @ one) == pytest.approx(_shoelace(QUAD), rel=1e-13)
+        nA = abs(A).max()
+        for c in range(2):
+            t = np.zeros(2 * N)
+            t[c * N:(c + 1) * N] = 1.0
+            assert np.abs(A @ t).max() <= 1e-12 * nA
+        r = np.concatenate([-P[:, 1], P[:, 0]])
+        rot_energy.append(r @ (A @ r))
+        A_ex, _ = fem.assemble(g, m)
+        assert abs(A_ex @ r).max() <= 1e-12 * abs(A_ex).max() * np.abs(r).max()
+        Af, ff = fem.system(g, m, loads, frozen_jacobian=True)
+        Ae, fe = fem.system(g, m, loads)
+        uf, ue = spla.spsolve(Af.tocsc(), ff), spla.spsolve(Ae.tocsc(), fe)
+        sol_diff.append(fem.energy_norm(Ae, uf - ue) / fem.energy_norm(Ae, ue))
+    for k in range(2):
+        assert 3.0 <= rot_energy[k] / rot_energy[k + 1] <= 5.0, rot_energy
+        assert 3.0 <= sol_diff[k] / sol_diff[k + 1] <= 5.0, sol_diff
+    assert sol_diff[-1] < 4e-3
