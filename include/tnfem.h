@@ -63,8 +63,17 @@ typedef struct {
                           {lo + sum_d xi_d edges[d] : xi in [0,1]^dim} (affine element maps, J
                           constant, Section 5.1; hi unused); faces are the images of the unit box's
                           faces; the material must be homogeneous (no E split inside the domain)
-                          and loads are gravity and uniform tractions only */
-  double edges[3][3];  /* mapped: edges[d] is the image of reference axis d (the columns of J) */
+                          and loads are gravity and uniform tractions only.
+                          2 (2D only, levels <= 12): the convex quadrilateral
+                          {lo + xi edges[0] + eta edges[1] + xi eta edges[2] : (xi, eta) in [0,1]^2}
+                          (corners lo, lo + edges[0], lo + edges[1], lo + edges[0] + edges[1] +
+                          edges[2]), every element's Jacobian frozen at its centre as in
+                          Algorithm 1; faces 0-3 are the sides xi = 0, xi = 1, eta = 0, eta = 1;
+                          two materials, gravity, tractions and Fourier loads are accepted.
+                          A quadrilateral whose det J changes sign or vanishes (not convex,
+                          degenerate) is refused with TNFEM_E_INVALID */
+  double edges[3][3];  /* mapped 1: edges[d] is the image of reference axis d (the columns of J);
+                          mapped 2: the bilinear map's coefficients as above (x, y entries) */
 } tnfem_grid;
 
 typedef struct {
@@ -207,10 +216,13 @@ tnfem_status tnfem_measure_fma_peak(tnfem_ctx* ctx, int precision, double* tflop
 
 /* Stiffness TT-operator with boundary conditions applied (Algorithm 1): A = P A0 P + s (I - P),
  * P the projector onto unknowns off the clamped faces, s the mean over components of A0's
- * diagonal at grid node (1,...,1).  Built on the host as exact Kronecker sums of 1D QTT
- * matrices (axis-aligned box => constant Jacobian, Section 5.1), then rounded on the device to
- * relative accuracy 1e-14.  Errors: TNFEM_E_INVALID for dim not in {2,3}, levels < 1 or > 20,
- * degenerate box, nu out of [0, 0.5). */
+ * diagonal at grid node (1,...,1).  Box and affine grids: built on the host as exact Kronecker
+ * sums of 1D QTT matrices (constant Jacobian, Section 5.1), then rounded on the device to
+ * relative accuracy 1e-14.  General quadrilaterals (mapped 2): the operator's 9-point stencil
+ * coefficients are formed densely on the host (O(4^levels) memory, 36 doubles per node), put in
+ * TT form by a TT-SVD on the device, multiplied by the per-axis offset automata and rounded on
+ * the device (relative accuracy ~1e-14).  Errors: TNFEM_E_INVALID for dim not in {2,3}, levels < 1
+ * or > 20 (> 12 for mapped 2), a degenerate box or quadrilateral, nu out of [0, 0.5). */
 tnfem_status tnfem_build_stiffness(tnfem_ctx* ctx, const tnfem_grid* grid,
                                    const tnfem_material* mat, tnfem_mpo** out);
 
@@ -223,8 +235,9 @@ tnfem_status tnfem_build_load(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfe
                               const tnfem_load* loads, int n_loads, tnfem_tt** out);
 
 /* Host-only variants of the three builders above: they run the exact host construction
- * (Kronecker sums of 1D QTT matrices, Section 5.2 / 5.3) without device rounding and without
- * touching any GPU, and copy the train into caller memory.  Call with cores == NULL to get
+ * (Kronecker sums of 1D QTT matrices, Section 5.2 / 5.3; for general quadrilaterals a host
+ * TT-SVD of the dense stencil coefficients, practical up to levels ~5) without device rounding
+ * and without touching any GPU, and copy the train into caller memory.  Call with cores == NULL to get
  * ncores, ranks (ncores+1 entries, caller provides >= 64) and modes (>= 63) for sizing; then
  * again with `cores` holding sum_k ranks[k]*modes[k]*(modes[k] for operators)*ranks[k+1]
  * doubles, laid out as in tnfem_tt_export / tnfem_mpo_export.  `shift` (nullable) receives the

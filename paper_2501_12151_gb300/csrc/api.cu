@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 
 #include "amen.h"
 #include "builder.h"
@@ -57,8 +58,10 @@ void check_grid(const tnfem_grid* g) {
   TN_REQUIRE(g, "grid is null");
   TN_REQUIRE(g->dim == 2 || g->dim == 3, "grid.dim must be 2 or 3");
   TN_REQUIRE(g->levels >= 1 && g->levels <= 20, "grid.levels must be in [1, 20]");
+  TN_REQUIRE(g->mapped >= 0 && g->mapped <= 2, "grid.mapped must be 0, 1 or 2");
   if (!g->mapped)
     for (int d = 0; d < g->dim; ++d) TN_REQUIRE(g->hi[d] > g->lo[d], "grid box is degenerate");
+  if (g->mapped == 2) check_quad(*g);
 }
 
 void check_material(const tnfem_material* m) {
@@ -107,6 +110,66 @@ tnfem_tt* upload_tt(tnfem_ctx* ctx, const HTrain& h, int ncomp, int dim) {
     throw;
   }
   return x;
+}
+
+// General quadrilateral (grid.mapped == 2): the dense stencil coefficients or load values are
+// built on the host, their TT comes from a TT-SVD on the device; the operator train (rank 9 x the
+// coefficients') is formed on the host and rounded on the device like the box operators.
+std::vector<int> quad_modes(int L, int first, int last) {
+  std::vector<int> m(1, first);
+  m.insert(m.end(), L, 4);
+  if (last) m.push_back(last);
+  return m;
+}
+
+HTrain download_train(tnfem_ctx* ctx, const tnfem_tt* x) {
+  HTrain h;
+  for (int k = 0; k < x->d; ++k) {
+    HCore c{x->r[k], x->n[k], x->r[k + 1], std::vector<double>((size_t)x->r[k] * x->n[k] * x->r[k + 1])};
+    TN_CHECK_CUDA(cudaMemcpyAsync(c.v.data(), x->core[k], c.v.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    h.c.push_back(std::move(c));
+  }
+  sync(ctx);
+  return h;
+}
+
+// a host train with arbitrary modes, rounded on the device and brought back
+HTrain round_on_device(tnfem_ctx* ctx, const HTrain& h, double eps) {
+  const int d = (int)h.c.size();
+  std::vector<int> n(d), r(d + 1, 1);
+  for (int k = 0; k < d; ++k) {
+    n[k] = h.c[k].N;
+    r[k + 1] = h.c[k].r1;
+  }
+  std::unique_ptr<tnfem_tt> x(tt_new(ctx, n, r));
+  for (int k = 0; k < d; ++k)
+    TN_CHECK_CUDA(cudaMemcpyAsync(x->core[k], h.c[k].v.data(), h.c[k].v.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  sync(ctx);
+  std::unique_ptr<tnfem_tt> y(tt_round(ctx, x.get(), eps, 1 << 20));
+  return download_train(ctx, y.get());
+}
+
+tnfem_mpo* build_quad_operator(tnfem_ctx* ctx, const tnfem_grid& g, const tnfem_material& mat, bool mass) {
+  HTrain coef;
+  {
+    std::vector<double> full;
+    quad_operator_coefficients(g, mat, mass, full, nullptr);
+    std::unique_ptr<tnfem_tt> ct(tt_from_full(ctx, full.data(), quad_modes(g.levels, 4, 9), 1e-14));
+    coef = download_train(ctx, ct.get());
+  }
+  const HTrain B = round_on_device(ctx, quad_stage_axis1(coef), 1e-14);
+  tnfem_mpo* raw = upload_mpo(ctx, quad_stage_axis0(B), 2, 2);
+  tnfem_mpo* A = nullptr;
+  try {
+    A = mpo_round(ctx, raw, 1e-14, 1 << 20);
+  } catch (...) {
+    delete raw;
+    throw;
+  }
+  delete raw;
+  return A;
 }
 
 // value of a train at one multi-index: product of core slices
@@ -366,6 +429,10 @@ tnfem_status tnfem_build_stiffness(tnfem_ctx* ctx, const tnfem_grid* grid, const
   return guard(ctx, [&] {
     check_grid(grid);
     check_material(mat);
+    if (grid->mapped == 2) {
+      *out = build_quad_operator(ctx, *grid, *mat, false);
+      return;
+    }
     double s = 0;
     HTrain h = stiffness_train(*grid, *mat, &s);
     tnfem_mpo* raw = upload_mpo(ctx, h, grid->dim, grid->dim);
@@ -386,6 +453,11 @@ tnfem_status tnfem_build_mass(tnfem_ctx* ctx, const tnfem_grid* grid, tnfem_mpo*
   *out = nullptr;
   return guard(ctx, [&] {
     check_grid(grid);
+    if (grid->mapped == 2) {
+      const tnfem_material any{{1.0, 1.0}, 1e300, 0.3};
+      *out = build_quad_operator(ctx, *grid, any, true);
+      return;
+    }
     HTrain h = mass_train(*grid);
     tnfem_mpo* raw = upload_mpo(ctx, h, grid->dim, grid->dim);
     tnfem_mpo* A = nullptr;
@@ -408,6 +480,12 @@ tnfem_status tnfem_build_load(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfe
     check_grid(grid);
     check_material(mat);
     TN_REQUIRE(n_loads >= 0 && (n_loads == 0 || loads), "loads array");
+    if (grid->mapped == 2) {
+      std::vector<double> full;
+      quad_load_values(*grid, *mat, loads, n_loads, full);
+      *out = tt_from_full(ctx, full.data(), quad_modes(grid->levels, 2, 0), 1e-14);
+      return;
+    }
     HTrain h = load_train(*grid, *mat, loads, n_loads);
     tnfem_tt* raw = upload_tt(ctx, h, grid->dim, grid->dim);
     tnfem_tt* f = nullptr;
@@ -572,7 +650,7 @@ tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_gr
     std::vector<double> h(D);
     for (int d = 0; d < D; ++d) h[d] = grid->mapped ? 1.0 / (N - 1) : (grid->hi[d] - grid->lo[d]) / (N - 1);
     double Jinv[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    if (grid->mapped) grid_affine_inverse(*grid, Jinv, nullptr);
+    if (grid->mapped == 1) grid_affine_inverse(*grid, Jinv, nullptr);
     const int ns = D == 2 ? 3 : 6;
     for (int64_t p = 0; p < n; ++p) {
       double gr[3][3] = {{0}};
@@ -584,6 +662,13 @@ tnfem_status tnfem_eval_strain(tnfem_ctx* ctx, const tnfem_tt* u, const tnfem_gr
             gr[c][d] += v * xi * std::pow(2.0, 1 - D) / h[d];
           }
         }
+      if (grid->mapped == 2) {
+        // the element's own Jacobian, frozen at its centre as in the assembly
+        double Ji[2][2];
+        quad_element_inverse(*grid, elems[p * D], elems[p * D + 1], Ji);
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j) Jinv[i][j] = Ji[i][j];
+      }
       if (grid->mapped) {
         double gp[3][3] = {{0}};
         for (int c = 0; c < D; ++c)

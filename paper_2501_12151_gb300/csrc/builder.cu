@@ -235,6 +235,55 @@ HTrain htt_from_vector(const std::vector<double>& v, int L) {
   return t;
 }
 
+// TT-SVD of a dense array (row-major, modes[0] slowest), left to right: each unfolding C (m x rest)
+// through the QR of its transpose and the SVD of the small factor, truncated to
+// eps / sqrt(d-1) ||v|| per bond.
+HTrain htt_svd(const std::vector<double>& v, const std::vector<int>& modes, double eps) {
+  const int d = (int)modes.size();
+  size_t total = 1;
+  for (int m : modes) total *= (size_t)m;
+  TN_REQUIRE(total == v.size(), "htt_svd: array size does not match the modes");
+  double nrm = 0;
+  for (double x : v) nrm += x * x;
+  const double delta = eps / std::sqrt((double)std::max(1, d - 1)) * std::sqrt(nrm);
+  HTrain t;
+  std::vector<double> C(v);
+  size_t rest = total;
+  int r = 1;
+  for (int k = 0; k < d - 1; ++k) {
+    rest /= (size_t)modes[k];
+    const int m = r * modes[k];
+    std::vector<double> U, S, Vt, next;
+    int keep, q;
+    if ((size_t)m <= rest) {
+      std::vector<double> Q, R;
+      hqr((int)rest, m, htranspose(m, (int)rest, C), Q, R);  // C^T = Q R, R: m x m
+      hsvd(m, m, htranspose(m, m, R), U, S, Vt);             // R^T = U S Vt, C = U S Vt Q^T
+      keep = truncation_rank(S, delta, 1 << 20);
+      q = m;
+      std::vector<double> SV((size_t)keep * m);
+      for (int i = 0; i < keep; ++i)
+        for (int j = 0; j < m; ++j) SV[(size_t)i * m + j] = S[i] * Vt[(size_t)i * m + j];
+      next = hmm(keep, m, (int)rest, SV.data(), htranspose((int)rest, m, Q).data());
+    } else {
+      hsvd(m, (int)rest, C, U, S, Vt);  // C = U S Vt directly (m > rest)
+      keep = truncation_rank(S, delta, 1 << 20);
+      q = (int)rest;
+      next.assign((size_t)keep * rest, 0.0);
+      for (int i = 0; i < keep; ++i)
+        for (size_t j = 0; j < rest; ++j) next[(size_t)i * rest + j] = S[i] * Vt[(size_t)i * rest + j];
+    }
+    HCore core{r, modes[k], keep, std::vector<double>((size_t)m * keep)};
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < keep; ++j) core.v[(size_t)i * keep + j] = U[(size_t)i * q + j];
+    t.c.push_back(core);
+    C.swap(next);
+    r = keep;
+  }
+  t.c.push_back(HCore{r, modes[d - 1], 1, C});
+  return t;
+}
+
 // ---- 1D tridiagonal operators in QTT ----------------------------------------------------------
 
 namespace {
@@ -551,7 +600,7 @@ HTrain combine_axes(const std::vector<HTrain>& axes, const std::vector<SepTerm>&
 
 // ---- elasticity operator terms -----------------------------------------------------------------
 
-static void lame(double E, double nu, int dim, bool plane_stress, double& lam, double& mu) {
+void lame(double E, double nu, int dim, bool plane_stress, double& lam, double& mu) {
   lam = E * nu / ((1 + nu) * (1 - 2 * nu));
   mu = E / (2 * (1 + nu));
   if (dim == 2 && plane_stress) lam = 2 * lam * mu / (lam + 2 * mu);
@@ -658,7 +707,22 @@ static std::vector<SepTerm> stiffness_terms_mapped(int D, double lam, double mu,
   return out;
 }
 
+// dense quadrilateral arrays (quad.cu) -> trains by TT-SVD on the host
+static std::vector<int> quad_modes(int L, int first, int last) {
+  std::vector<int> m(1, first);
+  m.insert(m.end(), L, 4);
+  if (last) m.push_back(last);
+  return m;
+}
+
 HTrain stiffness_train(const tnfem_grid& g_in, const tnfem_material& mat_in, double* shift_out) {
+  if (g_in.mapped == 2) {
+    std::vector<double> full;
+    quad_operator_coefficients(g_in, mat_in, false, full, shift_out);
+    HTrain B = quad_stage_axis1(htt_svd(full, quad_modes(g_in.levels, 4, 9), 1e-14));
+    B.round(1e-14, 1 << 20);
+    return quad_stage_axis0(B);
+  }
   const bool mapped = g_in.mapped != 0;
   Affine af;
   tnfem_material mat = mat_in;
@@ -742,6 +806,14 @@ HTrain stiffness_train(const tnfem_grid& g_in, const tnfem_material& mat_in, dou
 }
 
 HTrain mass_train(const tnfem_grid& g_in) {
+  if (g_in.mapped == 2) {
+    std::vector<double> full;
+    const tnfem_material any{{1.0, 1.0}, 1e300, 0.3};
+    quad_operator_coefficients(g_in, any, true, full, nullptr);
+    HTrain B = quad_stage_axis1(htt_svd(full, quad_modes(g_in.levels, 4, 9), 1e-14));
+    B.round(1e-14, 1 << 20);
+    return quad_stage_axis0(B);
+  }
   const double vol = g_in.mapped ? std::fabs(affine_of(g_in).det) : 1.0;
   const tnfem_grid g = g_in.mapped ? unit_box(g_in) : g_in;
   const int D = g.dim, L = g.levels, n = 1 << L;
@@ -780,6 +852,11 @@ struct VecCatalog {
 }  // namespace
 
 HTrain load_train(const tnfem_grid& g_in, const tnfem_material& mat, const tnfem_load* loads, int n_loads) {
+  if (g_in.mapped == 2) {
+    std::vector<double> full;
+    quad_load_values(g_in, mat, loads, n_loads, full);
+    return htt_svd(full, quad_modes(g_in.levels, 2, 0), 1e-15);
+  }
   // affine grid: body forces carry |det J|, a traction on a face the ratio of the face's measure
   // to the unit box face's (|J t| for the side along reference axis t in 2D, |J t1 x J t2| in 3D)
   const bool mapped = g_in.mapped != 0;

@@ -295,6 +295,10 @@ size_t mpo_bytes(const tnfem_mpo* A);
 
 // TT algebra on the device (tt_ops.cu)
 tnfem_tt* tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax);
+// TT-SVD of a dense host array (row-major, modes[0] slowest) on the device, left to right, each
+// unfolding through the QR of its transpose and the SVD of the small factor, truncated to
+// eps / sqrt(d-1) ||array|| per bond; unfoldings of at most 64 rows keep an identity core
+tnfem_tt* tt_from_full(tnfem_ctx* ctx, const double* host, const std::vector<int>& modes, double eps);
 tnfem_tt* tt_axpy(tnfem_ctx* ctx, const tnfem_tt* x, double beta, const tnfem_tt* y);
 tnfem_tt* mpo_apply(tnfem_ctx* ctx, const tnfem_mpo* A, const tnfem_tt* x);
 double tt_dot(tnfem_ctx* ctx, const tnfem_tt* x, const tnfem_tt* y);

@@ -2,6 +2,7 @@
 // Householder QR, then right-to-left truncated SVD, Section 4 Eq. qr), exact sums and
 // operator-times-train products, inner products, norms and the energy norm of a difference.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "internal.h"
@@ -368,6 +369,89 @@ tnfem_tt* tt_round(tnfem_ctx* ctx, const tnfem_tt* x, double eps, int rmax) {
     delete y;
     throw;
   }
+  return y;
+}
+
+tnfem_tt* tt_from_full(tnfem_ctx* ctx, const double* host, const std::vector<int>& modes, double eps) {
+  const int d = (int)modes.size();
+  TN_REQUIRE(d >= 1, "tt_from_full: no modes");
+  size_t total = 1;
+  for (int m : modes) total *= (size_t)m;
+  TN_REQUIRE(total <= (size_t)INT_MAX, "tt_from_full: array too large");
+  DArr<double> C(ctx, total);
+  TN_CHECK_CUDA(cudaMemcpyAsync(C.p, host, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  const double nrm = nrm2<double>(ctx, C.p, total);
+  const double delta = eps / std::sqrt((double)std::max(1, d - 1)) * nrm;
+  std::vector<DArr<double>> cores;
+  std::vector<int> r(d + 1, 1);
+  size_t rest = total;
+  int rk = 1;
+  for (int k = 0; k < d - 1; ++k) {
+    rest /= (size_t)modes[k];
+    const int m = rk * modes[k], ri = (int)rest;
+    if (m <= 64 && m <= ri) {
+      // an unfolding with at most 64 rows keeps the identity core (exact, rank = rows); the
+      // array itself is then already the next unfolding
+      std::vector<double> I((size_t)m * m, 0.0);
+      for (int i = 0; i < m; ++i) I[(size_t)i * m + i] = 1.0;
+      DArr<double> core(ctx, (size_t)m * m);
+      TN_CHECK_CUDA(cudaMemcpyAsync(core.p, I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      sync(ctx);
+      cores.push_back(std::move(core));
+      rk = r[k + 1] = m;
+      continue;
+    }
+    const int q = std::min(m, ri);
+    DArr<double> U(ctx, (size_t)m * q), Sd(ctx, q + 8), Vt(ctx, (size_t)q * q), next;
+    std::vector<double> S(q);
+    int keep;
+    if (m <= ri) {
+      // C (m x rest): C^T = Q R, R^T = U S Vt, so C = U S Vt Q^T
+      DArr<double> Q(ctx, rest * m), R(ctx, (size_t)m * m);
+      {
+        DArr<double> Ct(ctx, rest * m), qw(ctx, qr_work_elems(ri, m));
+        transpose2<double>(ctx, Ct.p, C.p, m, ri);
+        qr<double>(ctx, ri, m, Ct.p, Q.p, R.p, qw.p);
+      }
+      DArr<double> Rt(ctx, (size_t)m * m), sw(ctx, svd_work_elems(m, m));
+      transpose2<double>(ctx, Rt.p, R.p, m, m);
+      svd<double>(ctx, m, m, Rt.p, U.p, Sd.p, Vt.p, sw.p);
+      TN_CHECK_CUDA(cudaMemcpyAsync(S.data(), Sd.p, q * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+      keep = truncation_rank(S, delta, 1 << 20);
+      // next = diag(S) Vt[:keep] Q^T = (Q V[:, :keep] diag(S))^T, keep x rest
+      DArr<double> V(ctx, (size_t)m * m), VS(ctx, (size_t)m * keep);
+      transpose2<double>(ctx, V.p, Vt.p, m, m);
+      scale_cols(ctx, VS.p, V.p, m, m, keep, Sd.p);
+      next = DArr<double>(ctx, (size_t)keep * rest);
+      GemmDesc g{keep, ri, m, 1, 1, keep, 0, 1, m, 0, ri, 1, 0};
+      gemm<double>(ctx, g, 1.0, VS.p, Q.p, 0.0, next.p);
+    } else {
+      // more rows than columns: C = U S Vt directly
+      DArr<double> sw(ctx, svd_work_elems(m, ri));
+      svd<double>(ctx, m, ri, C.p, U.p, Sd.p, Vt.p, sw.p);
+      TN_CHECK_CUDA(cudaMemcpyAsync(S.data(), Sd.p, q * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+      keep = truncation_rank(S, delta, 1 << 20);
+      DArr<double> V(ctx, (size_t)ri * ri), VS(ctx, (size_t)ri * keep);
+      transpose2<double>(ctx, V.p, Vt.p, ri, ri);
+      scale_cols(ctx, VS.p, V.p, ri, ri, keep, Sd.p);
+      next = DArr<double>(ctx, (size_t)keep * rest);
+      transpose2<double>(ctx, next.p, VS.p, ri, keep);
+    }
+    // core = U[:, :keep]  (m x keep)
+    DArr<double> ones(ctx, keep), core(ctx, (size_t)m * keep);
+    fill<double>(ctx, ones.p, 1.0, keep);
+    scale_cols(ctx, core.p, U.p, m, q, keep, ones.p);
+    sync(ctx);
+    cores.push_back(std::move(core));
+    C = std::move(next);
+    rk = r[k + 1] = keep;
+  }
+  cores.push_back(std::move(C));
+  tnfem_tt* y = tt_new(ctx, modes, r);
+  for (int k = 0; k < d; ++k) copy<double>(ctx, y->core[k], cores[k].p, (size_t)r[k] * modes[k] * r[k + 1]);
+  sync(ctx);
   return y;
 }
 

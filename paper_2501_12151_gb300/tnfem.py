@@ -172,8 +172,16 @@ def c_grid(g: Grid) -> CGrid:
         cg.clamped[f] = 1 if (f < len(g.clamped) and g.clamped[f]) else 0
     cg.plane_stress = 1 if g.plane_stress else 0
     edges = getattr(g, "edges", None)
-    cg.mapped = 1 if edges is not None else 0
-    if edges is not None:
+    quad = getattr(g, "quad", None)
+    cg.mapped = 2 if quad is not None else (1 if edges is not None else 0)
+    if quad is not None:
+        # corners P0..P3 at unit-square (0,0), (1,0), (0,1), (1,1): lo = P0, edges = the bilinear
+        # map's coefficients a = P1 - P0, b = P2 - P0, c = P3 - P2 - P1 + P0
+        P = np.asarray(quad, dtype=float).reshape(4, -1)[:, :2]
+        cg.lo[0], cg.lo[1], cg.lo[2] = P[0, 0], P[0, 1], 0.0
+        for d, v in enumerate((P[1] - P[0], P[2] - P[0], P[3] - P[2] - P[1] + P[0])):
+            cg.edges[d][0], cg.edges[d][1], cg.edges[d][2] = float(v[0]), float(v[1]), 0.0
+    elif edges is not None:
         for d in range(min(3, len(edges))):
             for e in range(min(3, len(edges[d]))):
                 cg.edges[d][e] = float(edges[d][e])

@@ -138,3 +138,51 @@ def test_affine_domain_rejects_what_it_does_not_build():
         T.host_load(g, W.Material(), [W.Load(kind="fourier", amp=amp, wave=wave, phase=phase)])
     # a split outside the domain is a homogeneous material
     T.host_stiffness(g, W.Material(E=(1.0, 2.0), split_x=5.0))
+
+
+QUADS = [(2, ((0.0, 0.0), (1.0, 0.1), (0.2, 0.9), (1.3, 1.4)), (True, False, False, False), math.inf),
+         (3, ((0.0, 0.0), (1.0, 0.1), (0.2, 0.9), (1.3, 1.4)), (True, False, False, True), 0.6),
+         (4, ((0.3, -0.2), (2.0, 0.0), (0.5, 1.0), (1.6, 1.3)), (False, True, True, False), math.inf),
+         (3, ((0.0, 0.0), (0.0, 1.0), (1.0, 0.0), (1.2, 0.9)), (False, False, True, True), math.inf)]
+
+
+@pytest.mark.parametrize("levels,quad,clamped,split", QUADS)
+def test_host_builders_on_general_quadrilaterals_match_oracle(levels, quad, clamped, split):
+    """General convex quadrilaterals with each element's Jacobian frozen at its centre
+    (Algorithm 1): the host-built operator with its boundary-condition shift, the mass operator and
+    the load (gravity, a Fourier body force, tractions on the free sides) equal the oracle's
+    frozen-Jacobian element loop, two materials included; the last case is clockwise (det J < 0)."""
+    T = _lib()
+    g = W.Grid(dim=2, levels=levels, quad=quad, clamped=clamped)
+    m = W.Material(E=(2.0, 5.0), nu=0.3, split_x=split)
+    cores, s = T.host_stiffness(g, m)
+    K, M = fem.assemble(g, m, frozen_jacobian=True)
+    Aq = tt.matrix_to_qtt_order(fem.apply_bc(g, K), 2, levels)
+    assert np.abs(tt.mpo_full(cores) - Aq).max() <= 1e-12 * np.abs(Aq).max()
+    assert s == pytest.approx(fem.bc_shift(g, K), rel=1e-12)
+    Mq = tt.matrix_to_qtt_order(M, 2, levels)
+    assert np.abs(tt.mpo_full(T.host_mass(g)) - Mq).max() <= 1e-12 * np.abs(Mq).max()
+    amp, wave, phase = W.fourier_modes(1, 2, 2)
+    loads = [W.Load(kind="gravity", rho=3.0), W.Load(kind="fourier", amp=amp, wave=wave, phase=phase)] + [
+        W.Load(kind="traction", face=f, traction=(0.5, -1.0, 0.0)) for f in range(4) if not clamped[f]]
+    fv = fem.load_vector(g, m, loads, M) * np.tile(~fem.constrained_nodes(g), 2)
+    fq = tt.to_qtt_order(fv, 2, levels)
+    assert np.abs(tt.tt_full(T.host_load(g, m, loads)) - fq).max() <= 1e-12 * np.abs(fq).max()
+
+
+def test_general_quadrilateral_rejects_what_it_does_not_build():
+    """A non-convex or degenerate quadrilateral, more than 2^12 nodes per axis, a 3D grid and the
+    unit-square manufactured load are refused."""
+    T = _lib()
+    m = W.Material()
+    for quad in (((0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (0.2, 0.2)),      # re-entrant corner
+                 ((0.0, 0.0), (1.0, 0.0), (2.0, 0.0), (3.0, 0.0))):     # collinear
+        with pytest.raises(T.TnfemError):
+            T.host_stiffness(W.Grid(dim=2, levels=3, quad=quad), m)
+    good = ((0.0, 0.0), (1.0, 0.1), (0.2, 0.9), (1.3, 1.4))
+    with pytest.raises(T.TnfemError):
+        T.host_mass(W.Grid(dim=2, levels=13, quad=good))
+    with pytest.raises(T.TnfemError):
+        T.host_mass(W.Grid(dim=3, levels=2, quad=good))
+    with pytest.raises(T.TnfemError):
+        T.host_load(W.Grid(dim=2, levels=3, quad=good), m, [W.Load(kind="manufactured")])
