@@ -231,6 +231,22 @@ def cantilever_paper_2d(levels: int = 8, rank_cap: int = 64, tol: float = 1e-10,
     )
 
 
+QUAD_PLATE = ((0.0, 0.0), (1.0, 0.1), (0.2, 0.9), (1.3, 1.4))
+
+
+def quad_plate_2d(levels: int = 10, rank_cap: int = 64, tol: float = 1e-9, precision: str = "mixed-local") -> Problem:
+    """Steel on a convex, non-parallelogram quadrilateral (corners QUAD_PLATE at unit-square
+    (0,0), (1,0), (0,1), (1,1)), plane strain, clamped on the xi = 0 side, self-weight plus a
+    1 MN/m^2 downward traction on the xi = 1 side; element Jacobians frozen at the centres."""
+    return Problem(
+        name=f"2d-quad-plate-L{levels}",
+        grid=Grid(dim=2, levels=levels, quad=QUAD_PLATE, clamped=(True, False, False, False, False, False)),
+        material=Material(E=(210e9, 210e9), nu=0.3),
+        loads=[Load(kind="gravity", rho=7850.0), Load(kind="traction", face=FACE_XHI, traction=(0.0, -1e6, 0.0))],
+        opts=SolveOpts(tol=tol, rank_cap=rank_cap, precision=precision),
+    )
+
+
 def served_requests(seed: int = 0, n: int = 512, rate: float = 200.0):
     """Mixed request stream: per request, dimension, levels, material, load and rank cap."""
     arrivals = poisson_arrivals(seed, n, rate)
