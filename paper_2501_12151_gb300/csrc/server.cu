@@ -125,6 +125,13 @@ size_t serve_estimate_bytes(const tnfem_grid& g, const tnfem_solve_opts& o) {
     else if (L <= 5) build = 18.4 * GiB;
     else build = (18.4 + 3.4 * (L - 5)) * GiB * (L >= 8 ? 1.5 : 1.0);
   }
+  if (g.mapped == 2) {
+    // general quadrilateral: the build's device TT-SVD holds about four copies of the dense stencil
+    // coefficients (36 doubles per node), and the operator's ranks (up to ~100) are about three
+    // times the box operator's, which the sweep's environments scale with
+    build = 4.0 * 36.0 * 8.0 * std::pow(4.0, g.levels);
+    sweep *= 3.0;
+  }
   // + 128 MiB: a served 2D request (2^8, cap 16) held 174 MiB where a standalone solve held 57
   return (size_t)(1.25 * std::max(sweep, build) + 128.0 * MiB);
 }
