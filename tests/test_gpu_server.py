@@ -1,8 +1,9 @@
 """The serving loop (continuous batching of solve requests on one GPU).
 
-A mixed set of small requests (2D and 3D, different levels, materials, loads and rank caps) is
-served by three workers.  Each result must equal, to rounding, the same request served alone by
-an otherwise idle server with the same worker count (so the same kernels and grid sizes), and
+A mixed set of small requests (2D and 3D, box and general-quadrilateral domains, different levels,
+materials, loads and rank caps) is served by three workers.  Each result must equal, to rounding,
+the same request served alone by an otherwise idle server with the same worker count (so the same
+kernels and grid sizes), and
 must meet the solver's accuracy against the oracle's Galerkin solution.  Admission must keep the
 admitted estimates within the budget, each request's measured peak memory must stay within its
 estimate, and with room for several requests their runs must overlap in time.
@@ -35,6 +36,7 @@ def _requests():
     p = W.steel_plate_2d(levels=7, rank_cap=64, tol=1e-8, precision="mixed-local")
     p.loads = [W.Load(kind="traction", face=W.FACE_XHI, traction=(0.0, -2e6, 0.0))]
     out.append(p)
+    out.append(W.quad_plate_2d(levels=6, rank_cap=64, tol=1e-9, precision="mixed-local"))
     return out
 
 
@@ -67,7 +69,7 @@ def test_results_same_alone_and_in_the_mix(tn):
         assert da["info"]["sweeps"] == dm["info"]["sweeps"], pr.name
         ua, um = _dense(ca, pr), _dense(cm, pr)
         assert np.linalg.norm(um - ua) <= 1e-12 * np.linalg.norm(ua), pr.name
-        Abc, fv = fem.system(pr.grid, pr.material, pr.loads)
+        Abc, fv = fem.system(pr.grid, pr.material, pr.loads, frozen_jacobian=pr.grid.quad is not None)
         uh = fem.solve(Abc, fv)
         err = fem.energy_norm(Abc, um - uh) / fem.energy_norm(Abc, uh)
         bar = 1e-4 if "paper" in pr.name else 1e-6
