@@ -86,8 +86,11 @@ typedef enum {
   TNFEM_LOAD_GRAVITY = 0,      /* body force (0, -rho g) in 2D, (0, 0, -rho g) in 3D */
   TNFEM_LOAD_TRACTION = 1,     /* uniform traction vector on face `face` */
   TNFEM_LOAD_FOURIER = 2,      /* f_c(x) = scale * sum_m amp[c*n_modes+m] sin(pi wave_m . x + phase_m) */
-  TNFEM_LOAD_MANUFACTURED = 3  /* 2D unit square: body force and free-face tractions of
+  TNFEM_LOAD_MANUFACTURED = 3, /* 2D unit square: body force and free-face tractions of
                                   u* = (sin(pi x) sin(pi y), x(1-x) y(1-y)) */
+  TNFEM_LOAD_NODAL_TT = 4      /* the nodal values f0 of a body force given as a train (Section 5.3:
+                                  f = M f0, the Lagrange basis making nodal values the expansion
+                                  coefficients); device builder only */
 } tnfem_load_kind;
 
 typedef struct {
@@ -100,6 +103,9 @@ typedef struct {
   const int* wave;      /* FOURIER: [n_modes][dim] host array of integer wave numbers */
   const double* phase;  /* FOURIER: [n_modes] host array */
   double scale;         /* FOURIER */
+  const tnfem_tt* nodal; /* NODAL_TT: f0 as a train of the same context, laid out like the solution
+                            (component core of mode dim, then levels cores of mode 2^dim); read
+                            during the call only, not retained */
 } tnfem_load;
 
 /* FP64: every step in binary64.
@@ -230,7 +236,10 @@ tnfem_status tnfem_build_stiffness(tnfem_ctx* ctx, const tnfem_grid* grid,
 tnfem_status tnfem_build_mass(tnfem_ctx* ctx, const tnfem_grid* grid, tnfem_mpo** out);
 
 /* Load TT f = P (M f0 + sum_faces M_face t0) (Section 5.3), summed over n_loads loads and
- * rounded on the device to relative accuracy 1e-14. */
+ * rounded on the device to relative accuracy 1e-14.  A NODAL_TT load enters as P (M f0) with the
+ * grid's mass operator applied to the given train on the device (each product rounded at 1e-14).
+ * Errors: TNFEM_E_INVALID for a NODAL_TT load whose train is missing, belongs to another context or
+ * does not match the grid. */
 tnfem_status tnfem_build_load(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfem_material* mat,
                               const tnfem_load* loads, int n_loads, tnfem_tt** out);
 
@@ -466,7 +475,8 @@ tnfem_status tnfem_server_budget(const tnfem_server* s, size_t* bytes);
  * copies, environments, cores and local-solve workspace at the rank cap). */
 tnfem_status tnfem_serve_estimate(const tnfem_grid* grid, const tnfem_solve_opts* opts, size_t* bytes);
 /* Queue one request (arguments as for the builders and tnfem_solve; all host memory is copied,
- * Fourier arrays included).  *id identifies it.  TNFEM_E_INVALID after tnfem_server_stop began. */
+ * Fourier arrays included).  *id identifies it.  TNFEM_E_INVALID after tnfem_server_stop began and
+ * for a NODAL_TT load (its train lives in the caller's context, beyond the request's lifetime). */
 tnfem_status tnfem_submit(tnfem_server* s, const tnfem_grid* grid, const tnfem_material* mat,
                           const tnfem_load* loads, int n_loads, const tnfem_solve_opts* opts, uint64_t* id);
 /* Wait until request `id` is done (timeout_us < 0: no limit; TNFEM_E_TIMEOUT when it ran out) and

@@ -360,6 +360,8 @@ def nodal_body_force(grid: Grid, mat: Material, load: Load) -> np.ndarray:
         lam, mu = lame(mat.E[0], mat.nu, D, grid.plane_stress)
         f1, f2 = manufactured_force(P[:, 0], P[:, 1], lam, mu)
         f0[0], f0[1] = f1, f2
+    elif load.kind == "nodal":
+        f0[:] = np.asarray(load.values, dtype=float).reshape(D, N)   # given nodal values (Section 5.3)
     return f0.ravel()
 
 
@@ -389,7 +391,7 @@ def load_vector(grid: Grid, mat: Material, loads: Sequence[Load], M=None) -> np.
         _, M = assemble(grid, mat)
     f = np.zeros(M.shape[0])
     for ld in loads:
-        if ld.kind in ("gravity", "fourier", "manufactured"):
+        if ld.kind in ("gravity", "fourier", "manufactured", "nodal"):
             f += M @ nodal_body_force(grid, mat, ld)
         if ld.kind == "traction":
             f += face_mass(grid, ld.face) @ nodal_traction(grid, mat, ld, ld.face)

@@ -448,27 +448,41 @@ tnfem_status tnfem_build_stiffness(tnfem_ctx* ctx, const tnfem_grid* grid, const
   });
 }
 
+namespace {
+
+tnfem_mpo* mass_operator(tnfem_ctx* ctx, const tnfem_grid& g) {
+  if (g.mapped == 2) {
+    const tnfem_material any{{1.0, 1.0}, 1e300, 0.3};
+    return build_quad_operator(ctx, g, any, true);
+  }
+  std::unique_ptr<tnfem_mpo> raw(upload_mpo(ctx, mass_train(g), g.dim, g.dim));
+  return mpo_round(ctx, raw.get(), 1e-14, 1 << 20);
+}
+
+// f += P (M f0) for each nodal-train load (Section 5.3), on the device
+tnfem_tt* add_nodal_loads(tnfem_ctx* ctx, const tnfem_grid& g, const std::vector<const tnfem_tt*>& nodal,
+                          tnfem_tt* f_in) {
+  std::unique_ptr<tnfem_tt> f(f_in);
+  std::unique_ptr<tnfem_mpo> M(mass_operator(ctx, g));
+  std::unique_ptr<tnfem_mpo> P(upload_mpo(ctx, projector_train(g), g.dim, g.dim));
+  for (const tnfem_tt* f0 : nodal) {
+    std::unique_ptr<tnfem_tt> mf(mpo_apply(ctx, M.get(), f0));
+    std::unique_ptr<tnfem_tt> mfr(tt_round(ctx, mf.get(), 1e-14, 1 << 20));
+    std::unique_ptr<tnfem_tt> pmf(mpo_apply(ctx, P.get(), mfr.get()));
+    std::unique_ptr<tnfem_tt> sum(tt_axpy(ctx, f.get(), 1.0, pmf.get()));
+    f.reset(tt_round(ctx, sum.get(), 1e-14, 1 << 20));
+  }
+  return f.release();
+}
+
+}  // namespace
+
 tnfem_status tnfem_build_mass(tnfem_ctx* ctx, const tnfem_grid* grid, tnfem_mpo** out) {
   if (!ctx || !out) return TNFEM_E_INVALID;
   *out = nullptr;
   return guard(ctx, [&] {
     check_grid(grid);
-    if (grid->mapped == 2) {
-      const tnfem_material any{{1.0, 1.0}, 1e300, 0.3};
-      *out = build_quad_operator(ctx, *grid, any, true);
-      return;
-    }
-    HTrain h = mass_train(*grid);
-    tnfem_mpo* raw = upload_mpo(ctx, h, grid->dim, grid->dim);
-    tnfem_mpo* A = nullptr;
-    try {
-      A = mpo_round(ctx, raw, 1e-14, 1 << 20);
-    } catch (...) {
-      delete raw;
-      throw;
-    }
-    delete raw;
-    *out = A;
+    *out = mass_operator(ctx, *grid);
   });
 }
 
@@ -480,23 +494,32 @@ tnfem_status tnfem_build_load(tnfem_ctx* ctx, const tnfem_grid* grid, const tnfe
     check_grid(grid);
     check_material(mat);
     TN_REQUIRE(n_loads >= 0 && (n_loads == 0 || loads), "loads array");
+    // nodal-train loads go through the mass operator on the device; the rest is built on the host
+    std::vector<tnfem_load> analytic;
+    std::vector<const tnfem_tt*> nodal;
+    for (int i = 0; i < n_loads; ++i) {
+      if (loads[i].kind != TNFEM_LOAD_NODAL_TT) {
+        analytic.push_back(loads[i]);
+        continue;
+      }
+      const tnfem_tt* f0 = loads[i].nodal;
+      TN_REQUIRE(f0, "nodal-train load without a train");
+      TN_REQUIRE(f0->ctx == ctx, "nodal-train load: the train belongs to another context");
+      TN_REQUIRE(f0->d == grid->levels + 1 && f0->n[0] == grid->dim, "nodal-train load does not match the grid");
+      for (int k = 1; k < f0->d; ++k) TN_REQUIRE(f0->n[k] == (1 << grid->dim), "nodal-train load does not match the grid");
+      nodal.push_back(f0);
+    }
+    const int na = (int)analytic.size();
+    tnfem_tt* f = nullptr;
     if (grid->mapped == 2) {
       std::vector<double> full;
-      quad_load_values(*grid, *mat, loads, n_loads, full);
-      *out = tt_from_full(ctx, full.data(), quad_modes(grid->levels, 2, 0), 1e-14);
-      return;
+      quad_load_values(*grid, *mat, analytic.data(), na, full);
+      f = tt_from_full(ctx, full.data(), quad_modes(grid->levels, 2, 0), 1e-14);
+    } else {
+      std::unique_ptr<tnfem_tt> raw(upload_tt(ctx, load_train(*grid, *mat, analytic.data(), na), grid->dim, grid->dim));
+      f = tt_round(ctx, raw.get(), 1e-14, 1 << 20);
     }
-    HTrain h = load_train(*grid, *mat, loads, n_loads);
-    tnfem_tt* raw = upload_tt(ctx, h, grid->dim, grid->dim);
-    tnfem_tt* f = nullptr;
-    try {
-      f = tt_round(ctx, raw, 1e-14, 1 << 20);
-    } catch (...) {
-      delete raw;
-      throw;
-    }
-    delete raw;
-    *out = f;
+    *out = nodal.empty() ? f : add_nodal_loads(ctx, *grid, nodal, f);
   });
 }
 

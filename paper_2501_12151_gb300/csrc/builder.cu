@@ -805,6 +805,18 @@ HTrain stiffness_train(const tnfem_grid& g_in, const tnfem_material& mat_in, dou
   return combine_axes(axes, terms, D, true);
 }
 
+HTrain projector_train(const tnfem_grid& g) {
+  // P = I_c (x) P_0 (x) ... (x) P_{D-1}: the faces are index-space boundaries on every grid kind
+  const int D = g.dim, L = g.levels, n = 1 << L;
+  std::vector<HTrain> axes;
+  for (int d = 0; d < D; ++d)
+    axes.push_back(axis_operators(L, 0.0, 1.0, std::vector<double>(n - 1, 1.0), g.clamped[2 * d] != 0,
+                                  g.clamped[2 * d + 1] != 0, true).joint);
+  std::vector<SepTerm> terms;
+  for (int c = 0; c < D; ++c) terms.push_back(SepTerm{c, c, 1.0, std::vector<int>(D, OP_P)});
+  return combine_axes(axes, terms, D, true);
+}
+
 HTrain mass_train(const tnfem_grid& g_in) {
   if (g_in.mapped == 2) {
     std::vector<double> full;
@@ -971,6 +983,8 @@ HTrain load_train(const tnfem_grid& g_in, const tnfem_material& mat, const tnfem
           add(1, -(lam + 2 * mu), {massfn(0, quad), endvec(1, side)});
         }
       }
+    } else if (ld.kind == TNFEM_LOAD_NODAL_TT) {
+      throw Error(TNFEM_E_INVALID, "a nodal-train load is applied on the device (tnfem_build_load), not on the host");
     } else {
       throw Error(TNFEM_E_INVALID, "unknown load kind");
     }

@@ -48,6 +48,8 @@ void lame(double E, double nu, int dim, bool plane_stress, double& lam, double& 
 std::vector<SepTerm> stiffness_terms(int D, double lam, double mu);
 HTrain stiffness_train(const tnfem_grid& g, const tnfem_material& mat, double* shift_out);
 HTrain mass_train(const tnfem_grid& g);
+// the Dirichlet projector P (diagonal: 0 on the clamped faces' unknowns, 1 elsewhere) as an operator train
+HTrain projector_train(const tnfem_grid& g);
 // J^{-1} (row p, column e: d xi_p / d x_e) and det J of a mapped grid (grid.mapped != 0)
 void grid_affine_inverse(const tnfem_grid& g, double Jinv[3][3], double* det);
 HTrain load_train(const tnfem_grid& g, const tnfem_material& mat, const tnfem_load* loads,

@@ -315,6 +315,8 @@ tnfem_status tnfem_submit(tnfem_server* s, const tnfem_grid* grid, const tnfem_m
   r->opts = *opts;
   r->loads.assign(loads, loads + n_loads);
   for (auto& ld : r->loads) {
+    // a train lives in the caller's context and may be freed before the request runs
+    if (ld.kind == TNFEM_LOAD_NODAL_TT) return TNFEM_E_INVALID;
     if (ld.kind == TNFEM_LOAD_FOURIER) {
       if (ld.n_modes < 0 || (ld.n_modes > 0 && (!ld.amp || !ld.wave || !ld.phase))) return TNFEM_E_INVALID;
       r->amp.emplace_back(ld.amp, ld.amp + (size_t)grid->dim * ld.n_modes);

@@ -21,7 +21,7 @@ if not os.path.exists(_LIB_PATH):
 lib = C.CDLL(_LIB_PATH)
 
 STATUS = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "BUDGET", 7: "NUMERIC"}
-LOAD_KIND = {"gravity": 0, "traction": 1, "fourier": 2, "manufactured": 3}
+LOAD_KIND = {"gravity": 0, "traction": 1, "fourier": 2, "manufactured": 3, "nodal": 4}
 
 
 class TnfemError(RuntimeError):
@@ -43,7 +43,8 @@ class CMaterial(C.Structure):
 class CLoad(C.Structure):
     _fields_ = [("kind", C.c_int), ("rho", C.c_double), ("g", C.c_double), ("face", C.c_int),
                 ("traction", C.c_double * 3), ("n_modes", C.c_int), ("amp", C.POINTER(C.c_double)),
-                ("wave", C.POINTER(C.c_int)), ("phase", C.POINTER(C.c_double)), ("scale", C.c_double)]
+                ("wave", C.POINTER(C.c_int)), ("phase", C.POINTER(C.c_double)), ("scale", C.c_double),
+                ("nodal", C.c_void_p)]
 
 
 class COpts(C.Structure):
@@ -220,6 +221,12 @@ class _Loads:
                 c.amp = amp.ctypes.data_as(_pd)
                 c.wave = wave.ctypes.data_as(_pi)
                 c.phase = phase.ctypes.data_as(_pd)
+            if ld.kind == "nodal":
+                if ld.nodal is None or not getattr(ld.nodal, "h", None):
+                    raise ValueError("a nodal load needs a TT of the same context in Load.nodal")
+                self.keep.append(ld.nodal)
+                h = ld.nodal.h
+                c.nodal = h.value if isinstance(h, C.c_void_p) else h
         self.n = len(loads)
 
 

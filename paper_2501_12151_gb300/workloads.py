@@ -71,6 +71,9 @@ class Load:
       "fourier"      f_c(x) = scale * sum_m a[c,m] sin(pi k_m . x + phi_m)
       "manufactured" body force and free-face tractions of the manufactured field
                      u* = (sin(pi x) sin(pi y), x(1-x) y(1-y)) (2D, unit square)
+      "nodal"        a body force given by its nodal values f0 (Section 5.3): ``nodal`` is the
+                     library's train of them, ``values`` the same values densely (natural order,
+                     component-major) for the oracle
     """
     kind: str
     rho: float = 0.0
@@ -81,6 +84,8 @@ class Load:
     wave: Optional[np.ndarray] = None    # (n_modes, dim) integer wave numbers
     phase: Optional[np.ndarray] = None   # (n_modes,)
     scale: float = 1.0
+    nodal: Optional[object] = None       # "nodal": the library's TT of f0
+    values: Optional[np.ndarray] = None  # "nodal": f0 densely, natural order, component-major
 
 
 @dataclass

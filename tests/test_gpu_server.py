@@ -130,3 +130,19 @@ def test_wait_timeout_and_stop_with_queued_requests(tn):
     first = srv.wait(ids[0], take=False)[1]
     assert first["status"] in ("OK", "NOT_CONVERGED") and first["info"]["sweeps"] > 0
     srv.stop()                                            # the rest finish or are refused
+
+
+def test_nodal_train_loads_are_refused(tn):
+    """A request cannot carry a nodal-train load: the train lives in the caller's context and could
+    be freed before the request runs, so submit refuses it."""
+    pr = W.steel_plate_2d(levels=4, rank_cap=16, tol=1e-8, precision="mixed-local")
+    ctx = tn.Context(0)
+    rng = np.random.default_rng(0)
+    f0 = ctx.tt_import([rng.standard_normal((1, 2, 2))] + [rng.standard_normal((2, 4, 2)) for _ in range(3)] +
+                       [rng.standard_normal((2, 4, 1))])
+    srv = tn.Server(0, workers=1)
+    try:
+        with pytest.raises(tn.TnfemError):
+            srv.submit(pr.grid, pr.material, [W.Load(kind="nodal", nodal=f0)], pr.opts)
+    finally:
+        srv.stop()

@@ -370,6 +370,42 @@ def test_general_quadrilateral_solve_matches_galerkin(ctx, levels):
         np.testing.assert_allclose(got[p], want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["box", "box3d", "affine", "quad"])
+def test_nodal_train_load_matches_oracle(ctx, kind):
+    """A body force given by its nodal values as a train (Section 5.3: f = M f0, the solver's own
+    right-hand-side input), next to a gravity load: the device applies the grid's mass operator and
+    the Dirichlet projector to the train, and the result equals the oracle's P (M f0 + M g) on a
+    box (2D, 3D), a parallelogram and a general quadrilateral (frozen Jacobians).  A train that
+    does not match the grid is refused."""
+    from paper_2501_12151_gb300 import tnfem
+    L = 3 if kind == "box3d" else 5
+    if kind == "box":
+        g = W.Grid(dim=2, levels=L, lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 0.0), clamped=(True, False, False, True))
+    elif kind == "box3d":
+        g = W.Grid(dim=3, levels=L, lo=(0.0, 0.0, 0.0), hi=(1.0, 2.0, 0.5), clamped=(True, False, False, False, False, True))
+    elif kind == "affine":
+        g = W.Grid(dim=2, levels=L, lo=(0.2, -0.1, 0.3), edges=((1.5, 0.3), (0.6, 1.0)), clamped=(True, True, False, False))
+    else:
+        g = W.Grid(dim=2, levels=L, quad=QUAD, clamped=(False, True, True, False))
+    D = g.dim
+    m = W.Material(E=(2.0, 2.0), nu=0.3)
+    rng = np.random.default_rng(3)
+    cores = [rng.standard_normal((1, D, 3))] + [rng.standard_normal((3, 2 ** D, 3)) for _ in range(L - 1)] + \
+            [rng.standard_normal((3, 2 ** D, 1))]
+    f0 = ctx.tt_import(cores)
+    vals = tt.to_natural_order(tt.tt_full(cores), D, L)
+    loads = [W.Load(kind="gravity", rho=3.0), W.Load(kind="nodal", nodal=f0, values=vals)]
+    f = ctx.load(g, m, loads)
+    _, M = fem.assemble(g, m, frozen_jacobian=g.quad is not None)
+    fv = fem.load_vector(g, m, loads, M) * np.tile(~fem.constrained_nodes(g), D)
+    fq = tt.to_qtt_order(fv, D, L)
+    assert np.abs(tt.tt_full(f.cores()) - fq).max() <= 1e-12 * np.abs(fq).max()
+    short = ctx.tt_import(cores[:-2] + [rng.standard_normal((3, 2 ** D, 1))])
+    with pytest.raises(tnfem.TnfemError):
+        ctx.load(g, m, [W.Load(kind="nodal", nodal=short)])
+
+
 def test_checkpoint_and_resume(ctx):
     """Checkpoint / resume: a solve stopped after three sweeps is exported to host memory, imported
     into a fresh context and resumed as the start guess; the resumed solve reaches the Galerkin

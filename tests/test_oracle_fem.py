@@ -445,3 +445,34 @@ def test_quad_frozen_assembly_area_translations_and_convergence():
         assert 3.0 <= rot_energy[k] / rot_energy[k + 1] <= 5.0, rot_energy
         assert 3.0 <= sol_diff[k] / sol_diff[k + 1] <= 5.0, sol_diff
     assert sol_diff[-1] < 4e-3
+
+
+def test_nodal_load_integrates_affine_fields():
+    """f = M f0 from given nodal values (Section 5.3): for an affine f0 the component sums of f are
+    the exact integrals of f0, area times its value at the centroid, on a box, a parallelogram and
+    a general quadrilateral (exact assembly: det J is affine in xi, and the 2-point rule integrates
+    its product with the bilinear interpolant exactly) whose centroid is computed independently."""
+    a, b = np.array([0.7, -1.2]), np.array([[0.3, -0.5], [1.1, 0.4]])    # f0_c(x) = a_c + b_c . x
+    grids = [(W.Grid(dim=2, levels=4, lo=(0.2, -0.3, 0.0), hi=(1.7, 0.9, 0.0)), False),
+             (W.Grid(dim=2, levels=4, lo=(0.2, -0.3, 0.0), edges=SHEAR2), False),
+             (W.Grid(dim=2, levels=5, quad=QUAD), False)]
+    for g, frozen in grids:
+        P = fem.nodal_points(g)
+        vals = np.stack([a[c] + P @ b[c] for c in range(2)]).ravel()
+        _, M = fem.assemble(g, W.Material(), frozen_jacobian=frozen)
+        f = fem.load_vector(g, W.Material(), [W.Load(kind="nodal", values=vals)], M)
+        if g.quad is not None:
+            ring = [np.array(QUAD[i]) for i in (0, 1, 3, 2)]
+            cross = [ring[i][0] * ring[i - 3][1] - ring[i - 3][0] * ring[i][1] for i in range(4)]
+            area = 0.5 * sum(cross)
+            cen = sum((ring[i] + ring[i - 3]) * cross[i] for i in range(4)) / (6.0 * area)
+            area = abs(area)
+        elif g.edges is not None:
+            E = np.asarray(SHEAR2)
+            area, cen = abs(np.linalg.det(E)), np.array(g.lo[:2]) + 0.5 * (E[0] + E[1])
+        else:
+            area = (g.hi[0] - g.lo[0]) * (g.hi[1] - g.lo[1])
+            cen = 0.5 * (np.array(g.lo[:2]) + np.array(g.hi[:2]))
+        N = g.n ** 2
+        for c in range(2):
+            assert f[c * N:(c + 1) * N].sum() == pytest.approx(area * (a[c] + b[c] @ cen), rel=1e-12)
