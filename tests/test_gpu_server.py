@@ -100,9 +100,9 @@ def test_admission_keeps_estimates_within_budget(tn):
 
 
 def test_cancel_queued_request_and_stats(tn):
-    """A request still waiting for admission can be cancelled (a host-side fault injection of
-    SURVEY's "cancelled request"); the running one is not affected, and the queue statistics
-    count what waits and what runs."""
+    """A request still waiting for admission can be cancelled (a fault injected on the host: the
+    client gives up on a queued request); the running one is not affected, and the queue
+    statistics count what waits and what runs."""
     pr = W.steel_plate_2d(levels=8, rank_cap=64, tol=1e-9, precision="mixed-local")
     srv = tn.Server(0, workers=1)
     ids = [srv.submit(pr.grid, pr.material, pr.loads, pr.opts) for _ in range(3)]
