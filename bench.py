@@ -115,6 +115,11 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # nvidia-smi's start-up (driver queries) is kept out of the timed region: wait for its
+            # first sample (at most 5 s) before the caller starts timing
+            t0 = time.perf_counter()
+            while os.path.getsize(self.path) == 0 and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self

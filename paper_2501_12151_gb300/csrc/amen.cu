@@ -406,6 +406,12 @@ class Amen {
   DArr<float> PL32_, PR32_, g32_, y32_, Bx32_, r32_, p32_, Ap32_, z32_, ws32_, bjw32_;
   DArr<double> d64_;
   long long local_refines_ = 0;
+  // Per original core: consecutive visits whose first binary32 correction was confirmed (binary64
+  // residual) to have met its target with a factor-2 margin.  From two on, the confirming binary64
+  // matvec is skipped except on every fourth sweep; the sweep's own binary64 residual before each
+  // local solve still decides convergence, so a skipped check can cost sweeps, never accuracy.
+  std::vector<int> trust_;
+  int sweep_ = 0;
   long long breakdowns_ = 0;
   bool init_r_ready_ = false;  // r_ holds g - B x_k of the current core step (norm init_rn_)
   bool last_cg_converged_ = false;  // the last conjugate-gradient run met its tolerance
@@ -918,8 +924,11 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
     const bool have_r0 = init_r_ready_;  // the sweep step already formed r = g - B y for this y
     init_r_ready_ = false;
     bool stalled = false;
+    const int slot = oc(k);
+    if ((int)trust_.size() < d_) trust_.assign(d_, 0);
     for (int step = 0; step < 12; ++step) {
       double rn;
+      if (step == 1 && trust_[slot] >= 2 && sweep_ % 4 != 3) break;  // confirmation skipped
       if (step == 0 && have_r0) {
         rn = init_rn_;
       } else {
@@ -934,7 +943,11 @@ int Amen<T>::cg_local_mixed(int k, T* y, const T* g, double gnorm, double rtol) 
         sync(ctx_);
         rn = std::sqrt(rn2);
       }
-      if (!(rn > rtol * gnorm)) break;
+      if (!(rn > rtol * gnorm)) {
+        if (step == 1) trust_[slot] = rn <= 0.5 * rtol * gnorm ? trust_[slot] + 1 : 0;
+        break;
+      }
+      if (step > 0) trust_[slot] = 0;  // one binary32 correction was not enough
       if (step > 0 && !(rn < 0.5 * prev)) {  // stagnation: binary32 cannot reduce it further
         stalled = true;
         break;
@@ -1137,7 +1150,9 @@ void Amen<T>::run(AmenStats& st) {
   st = AmenStats();
   trace_ = getenv("TNFEM_TRACE") != nullptr;
   double res_hist[2] = {0.0, 0.0};  // largest local residuals of the two previous sweeps
+  trust_.assign(d, 0);
   for (int sweep = 0; sweep < prm_.max_sweeps; ++sweep) {
+    sweep_ = sweep;
     max_res_ = 0.0;
     max_dx_ = 0.0;
     for (int k = 0; k < d && !st.timed_out; ++k) {
