@@ -186,3 +186,33 @@ def test_general_quadrilateral_rejects_what_it_does_not_build():
         T.host_mass(W.Grid(dim=3, levels=2, quad=good))
     with pytest.raises(T.TnfemError):
         T.host_load(W.Grid(dim=2, levels=3, quad=good), m, [W.Load(kind="manufactured")])
+
+
+def test_nodal_train_load_is_refused_by_the_host_builder():
+    """A nodal-train load needs the device (mass operator times the train): the host-only builder
+    refuses it with an error status rather than ignoring it."""
+    import ctypes
+
+    T = _lib()
+
+    class FakeTT:                      # a non-null handle; the host builder must not touch it
+        h = ctypes.c_void_p(1)
+
+    g = W.Grid(dim=2, levels=3)
+    with pytest.raises(T.TnfemError):
+        T.host_load(g, W.Material(), [W.Load(kind="nodal", nodal=FakeTT())])
+
+
+def test_serving_estimate_covers_the_quadrilateral_build():
+    """The serving loop's memory estimate for a general quadrilateral covers the dense stencil
+    coefficients its build holds on the device (36 doubles per node, several copies), and grows
+    fourfold per level where those dominate."""
+    T = _lib()
+    e = {}
+    for L in (8, 10, 11, 12):
+        pr = W.quad_plate_2d(levels=L)
+        e[L] = T.serve_estimate(pr.grid, pr.opts)
+        assert e[L] >= 3 * 36 * 8 * 4 ** L
+    assert e[12] == pytest.approx(4 * e[11], rel=0.05)
+    box = W.steel_plate_2d(levels=10)
+    assert e[10] > T.serve_estimate(box.grid, box.opts)
