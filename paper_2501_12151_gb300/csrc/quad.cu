@@ -236,9 +236,8 @@ void quad_operator_coefficients(const tnfem_grid& g, const tnfem_material& mat, 
 namespace {
 
 // Offset automaton of one axis, most significant bit first: state 0 "j = i so far", 1 "j = i + 1"
-// (i ends in 0 1..1, j in 1 0..0), 2 "j = i - 1"; step(state, i bit, j bit) is the next state or -1.
-// For every next state and i bit exactly one (state, j bit) leads there, which is what keeps the
-// products below left-orthogonal wherever the coefficient cores are.
+// (i ends in 0 1..1, j in 1 0..0), 2 "j = i - 1"; step(state, i bit, j bit) is the next state or -1
+// (no continuation: the pair can no longer end at that offset).
 int step(int st, int bi, int bj) {
   if (st == 0) return bi == bj ? 0 : (bi == 0 ? 1 : 2);
   if (st == 1) return (bi == 1 && bj == 0) ? 1 : -1;
